@@ -1,0 +1,219 @@
+"""CPU oracle for the PRAND generators (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package.  The library under
+``paper_1307_5869_gb300`` never imports it, and the two share no code.
+
+The arithmetic lives in ``prand_oracle.c`` (plain C, one recurrence step at a
+time); this module only compiles it with gcc and marshals arguments through
+ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "prand_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+GENS = ["MT19937", "MRG32K3A", "LFSR113", "GM19", "GM29", "GM31", "GM55",
+        "GM61", "GQ58_1", "GQ58_3", "GQ58_4"]
+GEN_ID = {name: i for i, name in enumerate(GENS)}
+SEED_DEFAULT = 2**64 - 1
+NBIG = 8  # 512-bit jump offsets
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            vp = ctypes.c_void_p
+            L.orc_state_bytes.argtypes = [ctypes.c_int]
+            L.orc_seed.argtypes = [ctypes.c_int, ctypes.c_uint64, vp]
+            L.orc_next_u32.argtypes = [ctypes.c_int, vp]
+            L.orc_next_u32.restype = ctypes.c_uint32
+            L.orc_jump.argtypes = [ctypes.c_int, vp, u64p]
+            L.orc_block_length.argtypes = [ctypes.c_int, u64p]
+            L.orc_stream.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, vp]
+            L.orc_stream_range.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, vp]
+            for nm in ("orc_gen_u32", "orc_gen_f32", "orc_gen_f64"):
+                getattr(L, nm).argtypes = [ctypes.c_int, vp, vp, ctypes.c_uint64]
+            for nm in ("orc_gen_many_u32", "orc_gen_many_f32", "orc_gen_many_f64"):
+                getattr(L, nm).argtypes = [ctypes.c_int, vp, ctypes.c_uint64, vp, ctypes.c_uint64]
+            L.orc_u32_to_f32.argtypes = [ctypes.c_uint32]
+            L.orc_u32_to_f32.restype = ctypes.c_float
+            L.orc_u32_to_f64.argtypes = [ctypes.c_uint32]
+            L.orc_u32_to_f64.restype = ctypes.c_double
+            L.orc_mrg_to_f64.argtypes = [ctypes.c_uint32]
+            L.orc_mrg_to_f64.restype = ctypes.c_double
+            L.orc_mt_charpoly.argtypes = [u64p]
+            L.orc_mt_jump_poly.argtypes = [u64p, u64p]
+            L.orc_mt_x_pow2k.argtypes = [ctypes.c_int, u64p]
+            L.orc_mt_apply_poly.argtypes = [vp, u64p]
+            L.orc_lfsr_bits.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int]
+            L.orc_lfsr_comp_step.argtypes = [ctypes.c_uint32, ctypes.c_int]
+            L.orc_lfsr_comp_step.restype = ctypes.c_uint32
+            L.orc_lfsr_comp_jump.argtypes = [ctypes.c_uint32, ctypes.c_int, u64p]
+            L.orc_lfsr_comp_jump.restype = ctypes.c_uint32
+            L.orc_lfsr_param.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.orc_gm_param.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
+            L.orc_gm_matpow.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
+            L.orc_gm_point_step.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
+            L.orc_gm_point_jump.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p, u64p]
+            _lib = L
+    return _lib
+
+
+def big(n: int, words: int = NBIG):
+    """A non-negative Python int as a little-endian uint64 ctypes array."""
+    if n < 0 or n >= 1 << (64 * words):
+        raise ValueError("offset out of range")
+    arr = (ctypes.c_uint64 * words)()
+    for i in range(words):
+        arr[i] = (n >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
+    return arr
+
+
+def gid(gen) -> int:
+    return GEN_ID[gen] if isinstance(gen, str) else int(gen)
+
+
+class State:
+    """An oracle generator state (opaque bytes, layout fixed by the C file)."""
+
+    def __init__(self, gen, seed: int = SEED_DEFAULT, raw: bytes | None = None):
+        self.gen = gid(gen)
+        self.nbytes = lib().orc_state_bytes(self.gen)
+        self.buf = ctypes.create_string_buffer(self.nbytes)
+        if raw is not None:
+            ctypes.memmove(self.buf, raw, self.nbytes)
+        else:
+            lib().orc_seed(self.gen, ctypes.c_uint64(seed), self.buf)
+
+    @classmethod
+    def stream(cls, gen, seed: int, k: int) -> "State":
+        st = cls(gen, seed)
+        lib().orc_stream(st.gen, ctypes.c_uint64(seed), ctypes.c_uint64(k), st.buf)
+        return st
+
+    def copy(self) -> "State":
+        return State(self.gen, raw=self.buf.raw)
+
+    def raw(self) -> bytes:
+        return self.buf.raw
+
+    def jump(self, n: int) -> "State":
+        lib().orc_jump(self.gen, self.buf, big(n))
+        return self
+
+    def next(self) -> int:
+        return lib().orc_next_u32(self.gen, self.buf)
+
+    def u32(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint32)
+        lib().orc_gen_u32(self.gen, self.buf, out.ctypes.data, n)
+        return out
+
+    def f32(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.float32)
+        lib().orc_gen_f32(self.gen, self.buf, out.ctypes.data, n)
+        return out
+
+    def f64(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.float64)
+        lib().orc_gen_f64(self.gen, self.buf, out.ctypes.data, n)
+        return out
+
+
+def block_length(gen) -> int:
+    arr = (ctypes.c_uint64 * NBIG)()
+    lib().orc_block_length(gid(gen), arr)
+    return sum(int(arr[i]) << (64 * i) for i in range(NBIG))
+
+
+def gm_param(gen, name: str) -> int:
+    which = ["k", "q", "g", "v", "s", "t", "p", "L", "nmax"].index(name)
+    out = ctypes.c_uint64()
+    if lib().orc_gm_param(gid(gen), which, ctypes.byref(out)):
+        raise ValueError(gen)
+    return out.value
+
+
+class Streams:
+    """States of streams first..first+n-1 (back to back) for bulk generation."""
+
+    def __init__(self, gen, seed: int, first: int, n: int):
+        self.gen = gid(gen)
+        self.n = n
+        self.sb = lib().orc_state_bytes(self.gen)
+        self.buf = ctypes.create_string_buffer(self.sb * n)
+        rc = lib().orc_stream_range(self.gen, ctypes.c_uint64(seed), ctypes.c_uint64(first),
+                                    ctypes.c_uint64(n), self.buf)
+        if rc:
+            raise RuntimeError("oracle stream range failed")
+
+    def state(self, j: int) -> State:
+        return State(self.gen, raw=self.buf.raw[j * self.sb:(j + 1) * self.sb])
+
+    def generate(self, dtype: str, n_per: int) -> np.ndarray:
+        npdt = {"u32": np.uint32, "f32": np.float32, "f64": np.float64}[dtype]
+        out = np.empty(self.n * n_per, dtype=npdt)
+        fn = {"u32": lib().orc_gen_many_u32, "f32": lib().orc_gen_many_f32,
+              "f64": lib().orc_gen_many_f64}[dtype]
+        fn(self.gen, self.buf, ctypes.c_uint64(self.n), out.ctypes.data, ctypes.c_uint64(n_per))
+        return out.reshape(self.n, n_per)
+
+
+def mt_charpoly() -> int:
+    """The MT19937 characteristic polynomial as a Python int (bit i = x^i)."""
+    arr = (ctypes.c_uint64 * 313)()
+    deg = lib().orc_mt_charpoly(arr)
+    if deg != 19937:
+        raise RuntimeError(f"Berlekamp-Massey gave degree {deg}")
+    return sum(int(arr[i]) << (64 * i) for i in range(313))
+
+
+def mt_poly_words_to_int(arr) -> int:
+    return sum(int(arr[i]) << (64 * i) for i in range(313))
+
+
+def mt_x_pow2k(k: int) -> int:
+    arr = (ctypes.c_uint64 * 313)()
+    lib().orc_mt_x_pow2k(k, arr)
+    return mt_poly_words_to_int(arr)
+
+
+def mt_jump_poly(e: int) -> int:
+    arr = (ctypes.c_uint64 * 313)()
+    lib().orc_mt_jump_poly(big(e), arr)
+    return mt_poly_words_to_int(arr)
+
+
+def mt_apply_poly(st: State, poly: int) -> State:
+    arr = (ctypes.c_uint64 * 313)()
+    for i in range(313):
+        arr[i] = (poly >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
+    lib().orc_mt_apply_poly(st.buf, arr)
+    return st
