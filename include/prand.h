@@ -1,0 +1,169 @@
+/*
+ * prand.h -- C ABI of a GB300 (sm_103a) library that generates many independent
+ * streams of uniform pseudorandom numbers with the eleven generators of PRAND
+ * (Barash & Shchur, "PRAND: GPU accelerated parallel random number generation
+ * library", Comput. Phys. Commun. 185 (2014) 1343).
+ *
+ * The problem statement follows the paper: "fill an array in GPU memory with
+ * the next `length` numbers of a generator state" (Sec. 6; Sec. 7.5,
+ * rng_generate_gpu_array_, _float_, _double_) and "initialise stream number k
+ * by block splitting" (Sec. 5; Sec. 7.1, rng_init_sequence_; Table 4), here for
+ * n streams at once.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named dev_* are CUDA device pointers owned by the caller; host_*
+ *     are host pointers owned by the caller.  The library never frees them.
+ *   - A prand_stream_t is a cudaStream_t (NULL = the legacy default stream).
+ *   - Every call returns a prand_status_t.  Nothing aborts, nothing traps on
+ *     the device; a CUDA error is reported as PRAND_ERR_CUDA.
+ *   - Generation calls are asynchronous on the given stream; state creation,
+ *     stream initialisation, skip-ahead and state get/set complete before they
+ *     return.
+ *   - A handle is bound to the CUDA device that was current at prand_create;
+ *     every later call on it must be made with that device current.
+ *   - Calls on the same handle must not overlap (no internal locking per
+ *     handle).  Different handles are independent.
+ */
+#ifndef PRAND_H
+#define PRAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prand_handle_s *prand_handle_t;
+typedef void *prand_stream_t; /* a cudaStream_t */
+
+/* The eleven generators (Table 2).  The order is part of the ABI. */
+typedef enum {
+    PRAND_MT19937 = 0,  /* Matsumoto-Nishimura 1998; Sec. 5.4                       */
+    PRAND_MRG32K3A = 1, /* L'Ecuyer 1999; Sec. 5.2                                  */
+    PRAND_LFSR113 = 2,  /* L'Ecuyer 1999, four Tausworthe components; Sec. 5.3      */
+    PRAND_GM19 = 3,     /* torus-map ensembles, eq. (rec1) with Table 2's (k,q,g,v) */
+    PRAND_GM29 = 4,
+    PRAND_GM31 = 5,
+    PRAND_GM55 = 6,
+    PRAND_GM61 = 7,
+    PRAND_GQ58_1 = 8,
+    PRAND_GQ58_3 = 9,
+    PRAND_GQ58_4 = 10,
+    PRAND_NUM_GENERATORS = 11
+} prand_gen_t;
+
+typedef enum {
+    PRAND_OK = 0,
+    PRAND_ERR_ARG = 1,             /* null handle/pointer, bad enum, size overflow        */
+    PRAND_ERR_ALIGN = 2,           /* dev_out not aligned to its element size             */
+    PRAND_ERR_NOMEM = 3,           /* device or host allocation failed                    */
+    PRAND_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed         */
+    PRAND_ERR_STATE = 5,           /* call out of order (e.g. generate before init) or a
+                                      state blob of the wrong generator/size/version      */
+    PRAND_ERR_TIMEOUT = 6,         /* a bounded device wait gave up                       */
+    PRAND_WARN_STREAM_OVERLAP = 7  /* success, but first_stream + n_streams exceeds the
+                                      Table 4 capacity of the generator, so streams may
+                                      overlap within the generator's period             */
+} prand_status_t;
+
+/* Seed value meaning "the paper's default initial state" (rng_init_, Sec. 7.1):
+ * MT19937 init_genrand(5489); MRG32K3A all six words 12345; LFSR113 all four
+ * words 987654321; GM/GQ base pair (1, 1). */
+#define PRAND_SEED_DEFAULT UINT64_MAX
+
+/* Element types of prand_request_t.dtype. */
+#define PRAND_DTYPE_U32 0
+#define PRAND_DTYPE_F32 1
+#define PRAND_DTYPE_F64 2
+
+/* Create a handle for generator `gen` and build its base state on the current
+ * device (rng_init_, Sec. 7.1).  seed == PRAND_SEED_DEFAULT gives the default
+ * state; MT19937 seeds below 2^32 use init_genrand(seed), wider seeds
+ * init_by_array({lo32, hi32}); the other generators expand the seed with
+ * SplitMix64.  The first handle of a generator family on a device also builds
+ * that family's device jump tables (MT19937: the polynomials x^(2^b) mod phi,
+ * b < 512, Sec. 5.4).  On success *h owns its device memory until
+ * prand_destroy.  Errors: PRAND_ERR_ARG (h NULL, gen out of range),
+ * PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+prand_status_t prand_create(prand_handle_t *h, prand_gen_t gen, uint64_t seed);
+
+/* Allocate and initialise n_streams block-split streams: stream j of the handle
+ * is stream (first_stream + j) of the generator, i.e. the base state advanced
+ * by (first_stream + j) * L (Sec. 5; Table 4: the init_sequence variant with
+ * the most sequences: L = 6e6 GM19; 8e7 GM29, GM31, GQ58.x; 1e10 GM55, GM61;
+ * 2^34 LFSR113; 2^127 MRG32K3A; 2^432 MT19937).  The jump is exact for any
+ * 64-bit first_stream.  Replaces streams set up by an earlier call.
+ * Returns PRAND_WARN_STREAM_OVERLAP (after doing the work) when
+ * first_stream + n_streams exceeds the Table 4 number of sequences.
+ * Errors: PRAND_ERR_ARG (n_streams == 0 or first_stream + n_streams overflows),
+ * PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams);
+
+/* Write the next n_per_stream outputs of every stream, stream-major:
+ * dev_out[j * n_per_stream + i] = output i of stream j (rng_generate_gpu_array_,
+ * Sec. 6).  Each stream continues where the previous generate call on the
+ * handle stopped; the u32, f32 and f64 calls share that position.
+ * u32: the generator's 32-bit output (MRG32K3A: z in [1, m1]).
+ * f32: (u >> 8) * 2^-24 in [0, 1).
+ * f64: u * 2^-32 in [0, 1); MRG32K3A: z * RN(1 / (m1 + 1)) in (0, 1).
+ * dev_out must hold n_streams * n_per_stream elements and be aligned to its
+ * element size (16-byte alignment enables vector stores).  Any n_per_stream
+ * >= 0 is accepted (0 is a no-op).  Asynchronous on `stream`.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_STATE (no streams yet),
+ * PRAND_ERR_CUDA. */
+prand_status_t prand_generate_u32(prand_handle_t h, uint32_t *dev_out, uint64_t n_per_stream, prand_stream_t stream);
+prand_status_t prand_generate_f32(prand_handle_t h, float *dev_out, uint64_t n_per_stream, prand_stream_t stream);
+prand_status_t prand_generate_f64(prand_handle_t h, double *dev_out, uint64_t n_per_stream, prand_stream_t stream);
+
+/* Advance every stream of the handle by the 256-bit offset offset_le[0] +
+ * 2^64 offset_le[1] + 2^128 offset_le[2] + 2^192 offset_le[3] outputs
+ * (rng_skipahead_, Sec. 7.2; jump methods of Sec. 5.1-5.4).
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_STATE (no streams), PRAND_ERR_CUDA. */
+prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4]);
+
+/* Copy the full state of all streams into a host buffer (checkpoint), as a
+ * versioned blob that prand_set_state accepts on a handle of the same
+ * generator (the paper's state copy between host and device, Sec. 7).
+ * If host_buf is NULL, only *bytes is set to the size needed.
+ * Errors: PRAND_ERR_ARG (bytes NULL or *bytes too small), PRAND_ERR_STATE,
+ * PRAND_ERR_CUDA. */
+prand_status_t prand_get_state(prand_handle_t h, void *host_buf, size_t *bytes);
+prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t bytes);
+
+/* Number of streams of the handle and the per-stream output position
+ * (outputs produced since prand_init_streams, modulo 2^64).
+ * Errors: PRAND_ERR_ARG. */
+prand_status_t prand_query(prand_handle_t h, uint64_t *first_stream, uint64_t *n_streams, uint64_t *position);
+
+/* Free the handle's device memory.  h == NULL is a no-op. */
+prand_status_t prand_destroy(prand_handle_t h);
+
+/* A static English string for a status code. */
+const char *prand_status_string(prand_status_t status);
+
+/* Number of device kernels this library has launched in the process. */
+uint64_t prand_kernel_launches(void);
+
+/* One batched request: `length` outputs of stream `stream` of generator `gen`
+ * (seeded with the batch's seed), starting at the stream's beginning, written
+ * to dev_out (caller-owned, aligned to the element size of `dtype`). */
+typedef struct {
+    int32_t gen;      /* prand_gen_t */
+    int32_t dtype;    /* PRAND_DTYPE_U32 / _F32 / _F64 */
+    uint64_t stream;  /* any 64-bit stream index (block splitting, Table 4) */
+    uint64_t length;  /* outputs to write */
+    void *dev_out;    /* device pointer */
+} prand_request_t;
+
+/* Run n requests of mixed generators and uneven lengths (asynchronous on
+ * `stream`).  Each request's output equals prand_init_streams(stream, 1) then
+ * prand_generate_<dtype>(length) on a handle created with the same seed.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRAND_H */

@@ -1,0 +1,216 @@
+"""Python binding of the prand C ABI (``include/prand.h``).
+
+Argument marshalling only: every step of generation, jump-ahead and stream
+initialisation runs in the CUDA kernels of ``libprand_gb300.so``.  There is no
+CPU fallback; importing the binding without the built library raises.
+
+The functions keep the C names.  Device buffers are passed as integer device
+pointers (e.g. ``tensor.data_ptr()``) and streams as integer ``cudaStream_t``
+handles (e.g. ``torch.cuda.current_stream().cuda_stream``).  ``Generator`` is
+a small convenience wrapper over one handle that returns torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libprand_gb300.so")
+
+GENERATORS = ["MT19937", "MRG32K3A", "LFSR113", "GM19", "GM29", "GM31", "GM55",
+              "GM61", "GQ58_1", "GQ58_3", "GQ58_4"]
+GEN_ID = {g: i for i, g in enumerate(GENERATORS)}
+SEED_DEFAULT = 2**64 - 1
+DTYPE_U32, DTYPE_F32, DTYPE_F64 = 0, 1, 2
+
+PRAND_OK = 0
+PRAND_WARN_STREAM_OVERLAP = 7
+STATUS = {0: "PRAND_OK", 1: "PRAND_ERR_ARG", 2: "PRAND_ERR_ALIGN", 3: "PRAND_ERR_NOMEM",
+          4: "PRAND_ERR_CUDA", 5: "PRAND_ERR_STATE", 6: "PRAND_ERR_TIMEOUT",
+          7: "PRAND_WARN_STREAM_OVERLAP"}
+
+# Every symbol include/prand.h declares.
+EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_generate_f32",
+           "prand_generate_f64", "prand_skipahead", "prand_get_state", "prand_set_state",
+           "prand_query", "prand_destroy", "prand_status_string", "prand_kernel_launches",
+           "prand_batch_run"]
+
+
+class PrandError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_text(status)})")
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("gen", ctypes.c_int32), ("dtype", ctypes.c_int32), ("stream", ctypes.c_uint64),
+                ("length", ctypes.c_uint64), ("dev_out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """Load the shared library (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"prand CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        from . import build as _b
+        _b.build()
+    L = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    u64 = ctypes.c_uint64
+    L.prand_create.argtypes = [ctypes.POINTER(H), ctypes.c_int, u64]
+    L.prand_init_streams.argtypes = [H, u64, u64]
+    for nm in ("prand_generate_u32", "prand_generate_f32", "prand_generate_f64"):
+        getattr(L, nm).argtypes = [H, ctypes.c_void_p, u64, ctypes.c_void_p]
+    L.prand_skipahead.argtypes = [H, ctypes.POINTER(u64)]
+    L.prand_get_state.argtypes = [H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    L.prand_set_state.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+    L.prand_query.argtypes = [H, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.prand_destroy.argtypes = [H]
+    L.prand_status_string.argtypes = [ctypes.c_int]
+    L.prand_status_string.restype = ctypes.c_char_p
+    L.prand_kernel_launches.argtypes = []
+    L.prand_kernel_launches.restype = u64
+    L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
+    for nm in EXPORTS:
+        if nm not in ("prand_status_string", "prand_kernel_launches"):
+            getattr(L, nm).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _status_text(s: int) -> str:
+    try:
+        return load().prand_status_string(s).decode()
+    except Exception:  # pragma: no cover
+        return "?"
+
+
+def _check(status: int, where: str, allow_warn: bool = False) -> int:
+    if status == PRAND_OK or (allow_warn and status == PRAND_WARN_STREAM_OVERLAP):
+        return status
+    raise PrandError(status, where)
+
+
+def _gid(gen) -> int:
+    return GEN_ID[gen] if isinstance(gen, str) else int(gen)
+
+
+# ----------------------------------------------------------------- C names
+
+def prand_create(gen, seed: int = SEED_DEFAULT) -> int:
+    h = ctypes.c_void_p()
+    _check(load().prand_create(ctypes.byref(h), _gid(gen), ctypes.c_uint64(seed)), "prand_create")
+    return h.value
+
+
+def prand_init_streams(h: int, first_stream: int, n_streams: int) -> int:
+    return _check(load().prand_init_streams(h, first_stream, n_streams), "prand_init_streams", allow_warn=True)
+
+
+def prand_generate_u32(h: int, dev_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_u32(h, dev_out, n_per_stream, stream), "prand_generate_u32")
+
+
+def prand_generate_f32(h: int, dev_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_f32(h, dev_out, n_per_stream, stream), "prand_generate_f32")
+
+
+def prand_generate_f64(h: int, dev_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_f64(h, dev_out, n_per_stream, stream), "prand_generate_f64")
+
+
+def prand_skipahead(h: int, offset: int) -> None:
+    if offset < 0 or offset >= 1 << 256:
+        raise ValueError("offset must be in [0, 2^256)")
+    arr = (ctypes.c_uint64 * 4)(*[(offset >> (64 * i)) & 0xFFFFFFFFFFFFFFFF for i in range(4)])
+    _check(load().prand_skipahead(h, arr), "prand_skipahead")
+
+
+def prand_get_state(h: int) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(load().prand_get_state(h, None, ctypes.byref(n)), "prand_get_state")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().prand_get_state(h, buf, ctypes.byref(n)), "prand_get_state")
+    return buf.raw[:n.value]
+
+
+def prand_set_state(h: int, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().prand_set_state(h, buf, len(blob)), "prand_set_state")
+
+
+def prand_query(h: int):
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().prand_query(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "prand_query")
+    return a.value, b.value, c.value
+
+
+def prand_destroy(h: int) -> None:
+    if h:
+        _check(load().prand_destroy(h), "prand_destroy")
+
+
+def prand_status_string(status: int) -> str:
+    return _status_text(status)
+
+
+def prand_kernel_launches() -> int:
+    return int(load().prand_kernel_launches())
+
+
+def prand_batch_run(requests, seed: int, stream: int = 0) -> None:
+    """requests: iterable of (gen, dtype, stream_index, length, dev_ptr)."""
+    reqs = list(requests)
+    arr = (Request * max(1, len(reqs)))()
+    for i, (g, dt, s, n, p) in enumerate(reqs):
+        arr[i] = Request(_gid(g), dt, s, n, p)
+    _check(load().prand_batch_run(arr, len(reqs), ctypes.c_uint64(seed), stream), "prand_batch_run")
+
+
+# ----------------------------------------------------------------- wrapper
+
+class Generator:
+    """One handle: ``n_streams`` block-split streams of one generator."""
+
+    def __init__(self, gen, seed: int = SEED_DEFAULT, first_stream: int = 0, n_streams: int = 1):
+        self.gen = gen
+        self.h = prand_create(gen, seed)
+        self.status = prand_init_streams(self.h, first_stream, n_streams)
+        self.n_streams = n_streams
+
+    def close(self):
+        if self.h:
+            prand_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def generate(self, n_per_stream: int, dtype: str = "u32", out=None, stream=None):
+        import torch
+        tdt = {"u32": torch.int32, "f32": torch.float32, "f64": torch.float64}[dtype]
+        if out is None:
+            out = torch.empty((self.n_streams, n_per_stream), dtype=tdt, device="cuda")
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        fn = {"u32": prand_generate_u32, "f32": prand_generate_f32, "f64": prand_generate_f64}[dtype]
+        fn(self.h, out.data_ptr(), n_per_stream, st)
+        return out
+
+    def skipahead(self, offset: int):
+        prand_skipahead(self.h, offset)
+
+    def get_state(self) -> bytes:
+        return prand_get_state(self.h)
+
+    def set_state(self, blob: bytes):
+        prand_set_state(self.h, blob)
+        self.n_streams = prand_query(self.h)[1]

@@ -1,0 +1,381 @@
+// The prand_* C ABI: handle management, per-device jump tables, argument
+// checking, and dispatch to the generator families.
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "prand_internal.h"
+
+namespace prand {
+
+// family entry points (gen_*.cu)
+prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st);
+prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st);
+prand_status_t gm_build_table(int gen, uint64_t *tab, cudaStream_t st);
+prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                             cudaStream_t st);
+prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
+prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
+                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped);
+prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                       cudaStream_t st);
+prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
+prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out, int dtype,
+                      uint64_t nper, cudaStream_t st, bool *swapped);
+prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
+prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st);
+prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
+
+std::atomic<uint64_t> g_launches{ 0 };
+
+prand_status_t launch_check()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError() == cudaSuccess ? PRAND_OK : PRAND_ERR_CUDA;
+}
+
+size_t state_bytes_per_stream(int gen)
+{
+    if (gen == PRAND_MT19937) return kMtN * sizeof(uint32_t);
+    if (gen == PRAND_MRG32K3A) return 6 * sizeof(uint32_t);
+    if (gen == PRAND_LFSR113) return 4 * sizeof(uint32_t);
+    return 2 * (size_t)gm_params(gen).s * sizeof(uint64_t);
+}
+
+uint64_t table4_nmax(int gen)
+{
+    if (gen == PRAND_MT19937 || gen == PRAND_MRG32K3A) return 10000000000000000000ull;  // 1e19
+    if (gen == PRAND_LFSR113) return 3800000000000000000ull;                            // 3.8e18
+    return gm_params(gen).nmax;
+}
+
+// ------------------------------------------------------------------ tables
+namespace {
+constexpr int kMaxDevices = 64;
+DevTables g_tables[kMaxDevices];
+std::mutex g_tables_mu;
+}  // namespace
+
+prand_status_t get_tables(int gen, DevTables **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PRAND_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    DevTables &T = g_tables[dev];
+    T.device = dev;
+    if (!T.ready_basic) {
+        size_t mrg_b = (size_t)kJumpBits * 18 * sizeof(uint32_t);
+        size_t lfsr_b = (size_t)4 * kJumpBits * 32 * sizeof(uint32_t);
+        size_t gm_b = (size_t)kJumpBits * 4 * sizeof(uint64_t);
+        if (cudaMalloc(&T.mrg, mrg_b) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (cudaMalloc(&T.lfsr, lfsr_b) != cudaSuccess) return PRAND_ERR_NOMEM;
+        for (int g = 0; g < 8; ++g)
+            if (cudaMalloc(&T.gm[g], gm_b) != cudaSuccess) return PRAND_ERR_NOMEM;
+        prand_status_t s = mrg_build_table(T.mrg, 0);
+        if (s == PRAND_OK) s = lfsr_build_table(T.lfsr, 0);
+        for (int g = 0; g < 8 && s == PRAND_OK; ++g) s = gm_build_table(PRAND_GM19 + g, T.gm[g], 0);
+        if (s == PRAND_OK && cudaDeviceSynchronize() != cudaSuccess) s = PRAND_ERR_CUDA;
+        if (s != PRAND_OK) return s;
+        T.ready_basic = true;
+    }
+    if (gen == PRAND_MT19937 && !T.ready_mt) {
+        const uint32_t *host = mt_host_pow2_polys();
+        if (!host) return PRAND_ERR_STATE;
+        size_t bytes = (size_t)kMtPolyCount * kMtPolyWords * sizeof(uint32_t);
+        if (cudaMalloc(&T.mt, bytes) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (cudaMemcpy(T.mt, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
+        T.ready_mt = true;
+    }
+    *out = &T;
+    return PRAND_OK;
+}
+
+}  // namespace prand
+
+using namespace prand;
+
+struct prand_handle_s {
+    int gen = 0;
+    uint64_t seed = 0;
+    int device = 0;
+    DevTables *T = nullptr;
+    void *d_base = nullptr;
+    void *d_state = nullptr;
+    void *d_spare = nullptr;
+    uint64_t first = 0, n = 0;
+    uint64_t position = 0;
+    uint32_t mt_idx = kMtN;
+    cudaStream_t last_stream = 0;
+};
+
+namespace {
+
+constexpr uint32_t kBlobMagic = 0x444E5250u;  // "PRND"
+constexpr uint32_t kBlobVersion = 1;
+
+struct BlobHeader {
+    uint32_t magic, version;
+    int32_t gen;
+    uint32_t mt_idx;
+    uint64_t seed, first, n, position, state_bytes;
+};
+
+prand_status_t check_device(prand_handle_t h)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PRAND_ERR_CUDA;
+    return dev == h->device ? PRAND_OK : PRAND_ERR_STATE;
+}
+
+prand_status_t sync_last(prand_handle_t h)
+{
+    return cudaStreamSynchronize(h->last_stream) == cudaSuccess ? PRAND_OK : PRAND_ERR_CUDA;
+}
+
+void free_states(prand_handle_t h)
+{
+    if (h->d_state) cudaFree(h->d_state);
+    if (h->d_spare) cudaFree(h->d_spare);
+    h->d_state = h->d_spare = nullptr;
+    h->n = 0;
+}
+
+bool mul_overflows(uint64_t a, uint64_t b, uint64_t *r)
+{
+    return __builtin_mul_overflow(a, b, r);
+}
+
+prand_status_t generate_any(prand_handle_t h, void *out, int dtype, uint64_t nper, prand_stream_t stream)
+{
+    if (!h || !out) return PRAND_ERR_ARG;
+    size_t esz = dtype == PRAND_DTYPE_F64 ? 8 : 4;
+    if ((uintptr_t)out % esz) return PRAND_ERR_ALIGN;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    uint64_t total, bytes;
+    if (mul_overflows(h->n, nper, &total) || mul_overflows(total, esz, &bytes)) return PRAND_ERR_ARG;
+    if (nper == 0) return PRAND_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool swapped = false;
+    if (h->gen == PRAND_MT19937) s = mt_gen(h->d_state, h->n, &h->mt_idx, out, dtype, nper, st);
+    else if (is_gm(h->gen)) s = gm_gen(h->gen, h->T, h->d_state, h->d_spare, h->n, out, dtype, nper, st, &swapped);
+    else s = mrg_lfsr_gen(h->gen, h->T, h->d_state, h->d_spare, h->n, out, dtype, nper, st, &swapped);
+    if (s != PRAND_OK) return s;
+    if (swapped) { void *t = h->d_state; h->d_state = h->d_spare; h->d_spare = t; }
+    h->position += nper;
+    h->last_stream = st;
+    return PRAND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+prand_status_t prand_create(prand_handle_t *out, prand_gen_t gen, uint64_t seed)
+{
+    if (!out) return PRAND_ERR_ARG;
+    *out = nullptr;
+    if ((int)gen < 0 || (int)gen >= PRAND_NUM_GENERATORS) return PRAND_ERR_ARG;
+    prand_handle_t h = new (std::nothrow) prand_handle_s;
+    if (!h) return PRAND_ERR_NOMEM;
+    h->gen = (int)gen;
+    h->seed = seed;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return PRAND_ERR_CUDA; }
+    prand_status_t s = get_tables(h->gen, &h->T);
+    if (s != PRAND_OK) { delete h; return s; }
+    if (cudaMalloc(&h->d_base, state_bytes_per_stream(h->gen)) != cudaSuccess) { delete h; return PRAND_ERR_NOMEM; }
+    if (h->gen == PRAND_MT19937) s = mt_seed(seed, h->d_base, 0);
+    else if (is_gm(h->gen)) s = gm_seed(h->gen, h->T, seed, h->d_base, 0);
+    else s = mrg_lfsr_seed(h->gen, seed, h->d_base, 0);
+    if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
+    if (s != PRAND_OK) { cudaFree(h->d_base); delete h; return s; }
+    *out = h;
+    return PRAND_OK;
+}
+
+prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams)
+{
+    if (!h || n_streams == 0) return PRAND_ERR_ARG;
+    uint64_t last;
+    if (__builtin_add_overflow(first_stream, n_streams - 1, &last)) return PRAND_ERR_ARG;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    if ((s = sync_last(h)) != PRAND_OK) return s;
+    free_states(h);
+    uint64_t bytes;
+    if (mul_overflows(n_streams, state_bytes_per_stream(h->gen), &bytes)) return PRAND_ERR_ARG;
+    if (cudaMalloc(&h->d_state, bytes) != cudaSuccess) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
+    if (h->gen != PRAND_MT19937 && cudaMalloc(&h->d_spare, bytes) != cudaSuccess) {
+        h->d_spare = nullptr;
+        free_states(h);
+        return PRAND_ERR_NOMEM;
+    }
+    if (h->gen == PRAND_MT19937) s = mt_init(h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
+    else if (is_gm(h->gen)) s = gm_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
+    else s = mrg_lfsr_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
+    if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
+    if (s != PRAND_OK) { free_states(h); return s; }
+    h->first = first_stream;
+    h->n = n_streams;
+    h->position = 0;
+    h->mt_idx = kMtN;
+    h->last_stream = 0;
+    // Table 4 capacity: the last stream index must stay below the number of sequences
+    if (last >= table4_nmax(h->gen)) return PRAND_WARN_STREAM_OVERLAP;
+    return PRAND_OK;
+}
+
+prand_status_t prand_generate_u32(prand_handle_t h, uint32_t *dev_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_any(h, dev_out, PRAND_DTYPE_U32, n_per_stream, stream);
+}
+
+prand_status_t prand_generate_f32(prand_handle_t h, float *dev_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_any(h, dev_out, PRAND_DTYPE_F32, n_per_stream, stream);
+}
+
+prand_status_t prand_generate_f64(prand_handle_t h, double *dev_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_any(h, dev_out, PRAND_DTYPE_F64, n_per_stream, stream);
+}
+
+prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4])
+{
+    if (!h || !offset_le) return PRAND_ERR_ARG;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    if ((s = sync_last(h)) != PRAND_OK) return s;
+    U256 off;
+    for (int i = 0; i < 4; ++i) off.w[i] = offset_le[i];
+    if (!(off.w[0] | off.w[1] | off.w[2] | off.w[3])) return PRAND_OK;
+    if (h->gen == PRAND_MT19937) s = mt_skip(h->T, h->d_state, h->n, &h->mt_idx, off, 0);
+    else if (is_gm(h->gen)) s = gm_skip(h->gen, h->T, h->d_state, h->n, off, 0);
+    else s = mrg_lfsr_skip(h->gen, h->T, h->d_state, h->n, off, 0);
+    if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
+    if (s == PRAND_OK) h->position += off.w[0];
+    return s;
+}
+
+prand_status_t prand_get_state(prand_handle_t h, void *host_buf, size_t *bytes)
+{
+    if (!h || !bytes) return PRAND_ERR_ARG;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    size_t sb = (size_t)h->n * state_bytes_per_stream(h->gen);
+    size_t need = sizeof(BlobHeader) + sb;
+    if (!host_buf) { *bytes = need; return PRAND_OK; }
+    if (*bytes < need) { *bytes = need; return PRAND_ERR_ARG; }
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    if ((s = sync_last(h)) != PRAND_OK) return s;
+    BlobHeader hd = { kBlobMagic, kBlobVersion, h->gen, h->mt_idx, h->seed, h->first, h->n, h->position, sb };
+    memcpy(host_buf, &hd, sizeof hd);
+    if (cudaMemcpy((char *)host_buf + sizeof hd, h->d_state, sb, cudaMemcpyDeviceToHost) != cudaSuccess) return PRAND_ERR_CUDA;
+    *bytes = need;
+    return PRAND_OK;
+}
+
+prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t bytes)
+{
+    if (!h || !host_buf || bytes < sizeof(BlobHeader)) return PRAND_ERR_ARG;
+    BlobHeader hd;
+    memcpy(&hd, host_buf, sizeof hd);
+    if (hd.magic != kBlobMagic || hd.version != kBlobVersion || hd.gen != h->gen || hd.n == 0) return PRAND_ERR_STATE;
+    uint64_t sb;
+    if (mul_overflows(hd.n, state_bytes_per_stream(h->gen), &sb) || sb != hd.state_bytes ||
+        bytes != sizeof hd + sb || hd.mt_idx > (uint32_t)kMtN)
+        return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    if ((s = sync_last(h)) != PRAND_OK) return s;
+    if (h->n != hd.n) {
+        free_states(h);
+        if (cudaMalloc(&h->d_state, sb) != cudaSuccess) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
+        if (h->gen != PRAND_MT19937 && cudaMalloc(&h->d_spare, sb) != cudaSuccess) {
+            h->d_spare = nullptr;
+            free_states(h);
+            return PRAND_ERR_NOMEM;
+        }
+    }
+    if (cudaMemcpy(h->d_state, (const char *)host_buf + sizeof hd, sb, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
+    h->first = hd.first;
+    h->n = hd.n;
+    h->position = hd.position;
+    h->mt_idx = hd.mt_idx;
+    return PRAND_OK;
+}
+
+prand_status_t prand_query(prand_handle_t h, uint64_t *first_stream, uint64_t *n_streams, uint64_t *position)
+{
+    if (!h) return PRAND_ERR_ARG;
+    if (first_stream) *first_stream = h->first;
+    if (n_streams) *n_streams = h->n;
+    if (position) *position = h->position;
+    return PRAND_OK;
+}
+
+prand_status_t prand_destroy(prand_handle_t h)
+{
+    if (!h) return PRAND_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->last_stream);
+    free_states(h);
+    if (h->d_base) cudaFree(h->d_base);
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    delete h;
+    return PRAND_OK;
+}
+
+const char *prand_status_string(prand_status_t s)
+{
+    switch (s) {
+    case PRAND_OK: return "success";
+    case PRAND_ERR_ARG: return "invalid argument";
+    case PRAND_ERR_ALIGN: return "output pointer not aligned to its element size";
+    case PRAND_ERR_NOMEM: return "out of memory";
+    case PRAND_ERR_CUDA: return "CUDA error";
+    case PRAND_ERR_STATE: return "invalid handle state or state blob";
+    case PRAND_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PRAND_WARN_STREAM_OVERLAP: return "streams beyond the generator's Table 4 capacity may overlap";
+    default: return "unknown status";
+    }
+}
+
+uint64_t prand_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream)
+{
+    // Reference form of the batch: one handle per request, each request its own
+    // launches.  (The fused persistent form replaces this body.)
+    if (!reqs && n) return PRAND_ERR_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        const prand_request_t &r = reqs[i];
+        if (r.gen < 0 || r.gen >= PRAND_NUM_GENERATORS || r.dtype < 0 || r.dtype > 2 || (!r.dev_out && r.length))
+            return PRAND_ERR_ARG;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        const prand_request_t &r = reqs[i];
+        if (!r.length) continue;
+        prand_handle_t h;
+        prand_status_t s = prand_create(&h, (prand_gen_t)r.gen, seed);
+        if (s != PRAND_OK) return s;
+        s = prand_init_streams(h, r.stream, 1);
+        if (s != PRAND_OK && s != PRAND_WARN_STREAM_OVERLAP) { prand_destroy(h); return s; }
+        s = generate_any(h, r.dev_out, r.dtype, r.length, stream);
+        if (s == PRAND_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = PRAND_ERR_CUDA;
+        prand_destroy(h);
+        if (s != PRAND_OK) return s;
+    }
+    return PRAND_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Device helpers shared by the generation and jump kernels: exact modular
+// arithmetic for the moduli of Sec. 5.1-5.2, SplitMix64 seed expansion, the
+// float epilogue, and vectorised output emission.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prand_internal.h"
+
+namespace prand {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------- SplitMix64
+// Seed expansion (Steele, Lea & Flood 2014); the same published definition on
+// both sides of any comparison, used only to turn a 64-bit seed into states.
+__host__ __device__ inline uint64_t splitmix64_next(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- mod m1, m2
+// a * b mod m for m = 2^32 - c (c = 209 or 22853), a, b < 2^32: fold the high
+// word twice with 2^32 = c (mod m).
+template <uint32_t C>
+__device__ __forceinline__ uint32_t mulmod_2p32_minus(uint32_t a, uint32_t b)
+{
+    constexpr uint64_t m = (1ull << 32) - C;
+    uint64_t p = (uint64_t)a * b;
+    uint64_t t = (p & 0xFFFFFFFFull) + (uint64_t)C * (p >> 32);   // < 2^32 (1 + C)
+    t = (t & 0xFFFFFFFFull) + (uint64_t)C * (t >> 32);            // < 2^32 + C (C+1)
+    if (t >= m) t -= m;
+    return (uint32_t)t;
+}
+
+__device__ __forceinline__ uint32_t addmod_u32(uint32_t a, uint32_t b, uint32_t m)
+{
+    uint64_t s = (uint64_t)a + b;
+    return (uint32_t)(s >= m ? s - m : s);
+}
+
+// ---------------------------------------------------------------- mod p (GM/GQ)
+// Full products of residues modulo the five primes of Table 2.
+template <int KIND>
+__device__ __forceinline__ uint64_t reduce_prod(uint64_t lo, uint64_t hi);
+
+// p = 2^19 - 1: product < 2^38 (hi = 0)
+template <>
+__device__ __forceinline__ uint64_t reduce_prod<P19>(uint64_t lo, uint64_t)
+{
+    constexpr uint64_t p = (1ull << 19) - 1;
+    uint64_t r = (lo & p) + (lo >> 19);   // < 2^20
+    r = (r & p) + (r >> 19);              // <= p + 1
+    return r >= p ? r - p : r;
+}
+// p = 2^29 - 3: product < 2^58 (hi = 0); 2^29 = 3 (mod p)
+template <>
+__device__ __forceinline__ uint64_t reduce_prod<P29>(uint64_t lo, uint64_t)
+{
+    constexpr uint64_t p = (1ull << 29) - 3, m = (1ull << 29) - 1;
+    uint64_t r = (lo & m) + 3 * (lo >> 29);   // < 2^29 + 3 * 2^29
+    r = (r & m) + 3 * (r >> 29);              // < 2^29 + 12
+    return r >= p ? r - p : r;
+}
+// p = 2^31 - 1: product < 2^62 (hi = 0)
+template <>
+__device__ __forceinline__ uint64_t reduce_prod<P31>(uint64_t lo, uint64_t)
+{
+    constexpr uint64_t p = (1ull << 31) - 1;
+    uint64_t r = (lo & p) + (lo >> 31);   // < 2^32
+    r = (r & p) + (r >> 31);
+    return r >= p ? r - p : r;
+}
+// p = 2^51 - 129: product < 2^102; 2^51 = 129 (mod p)
+template <>
+__device__ __forceinline__ uint64_t reduce_prod<P51>(uint64_t lo, uint64_t hi)
+{
+    constexpr uint64_t p = (1ull << 51) - 129, m = (1ull << 51) - 1;
+    uint64_t h = (hi << 13) | (lo >> 51);         // < 2^51
+    uint64_t r = (lo & m) + 129 * h;              // < 2^51 + 2^59
+    r = (r & m) + 129 * (r >> 51);                // < 2^51 + 2^17
+    return r >= p ? r - p : r;
+}
+// p = 2^61 - 1: product < 2^122
+template <>
+__device__ __forceinline__ uint64_t reduce_prod<P61>(uint64_t lo, uint64_t hi)
+{
+    constexpr uint64_t p = (1ull << 61) - 1;
+    uint64_t r = (lo & p) + ((hi << 3) | (lo >> 61));   // < 2^62
+    r = (r & p) + (r >> 61);
+    return r >= p ? r - p : r;
+}
+
+template <int KIND>
+__device__ __forceinline__ uint64_t mulmod_p(uint64_t a, uint64_t b)
+{
+    if (KIND == P51 || KIND == P61) return reduce_prod<KIND>(a * b, __umul64hi(a, b));
+    return reduce_prod<KIND>(a * b, 0);
+}
+
+template <int KIND>
+__device__ __forceinline__ uint64_t prime_of()
+{
+    return KIND == P19 ? (1ull << 19) - 1 : KIND == P29 ? (1ull << 29) - 3 : KIND == P31 ? (1ull << 31) - 1
+         : KIND == P51 ? (1ull << 51) - 129 : (1ull << 61) - 1;
+}
+
+template <int KIND>
+__device__ __forceinline__ uint64_t addmod_p(uint64_t a, uint64_t b)
+{
+    uint64_t s = a + b;   // both < p < 2^62
+    return s >= prime_of<KIND>() ? s - prime_of<KIND>() : s;
+}
+
+// ---------------------------------------------------------------- floats
+// f32 = (u >> 8) * 2^-24: the 24-bit integer converts exactly, the scale is a power of two.
+__device__ __forceinline__ float u32_to_f32(uint32_t u) { return __uint2float_rn(u >> 8) * 0x1p-24f; }
+
+// f64 = u * 2^-32, assembled from the bits (exact) to stay off the FP64 pipe.
+__device__ __forceinline__ double u32_to_f64(uint32_t u)
+{
+    if (u == 0) return 0.0;
+    int lz = __clz(u);                         // MSB at bit 31 - lz
+    uint32_t m = (u << lz) << 1;               // fraction bits, MSB dropped
+    uint32_t hi = ((uint32_t)(1022 - lz) << 20) | (m >> 12);
+    uint32_t lo = m << 20;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// MRG32K3A f64 = z * RN(1 / (m1 + 1)): one round-to-nearest multiply.
+__device__ __forceinline__ double mrg_to_f64(uint32_t z)
+{
+    constexpr double kNorm = 1.0 / 4294967088.0;
+    return __dmul_rn((double)z, kNorm);
+}
+
+// ---------------------------------------------------------------- output
+// Conversion of one 32-bit output to the requested element type.
+template <typename OutT, bool MRG = false>
+struct Cvt;
+template <bool MRG>
+struct Cvt<uint32_t, MRG> { __device__ __forceinline__ static uint32_t f(uint32_t u) { return u; } };
+template <bool MRG>
+struct Cvt<float, MRG> { __device__ __forceinline__ static float f(uint32_t u) { return u32_to_f32(u); } };
+template <>
+struct Cvt<double, false> { __device__ __forceinline__ static double f(uint32_t u) { return u32_to_f64(u); } };
+template <>
+struct Cvt<double, true> { __device__ __forceinline__ static double f(uint32_t u) { return mrg_to_f64(u); } };
+
+// Store four consecutive elements at p (16-byte aligned for 4-byte types,
+// 32-byte aligned for doubles when vec is true).
+template <typename OutT>
+__device__ __forceinline__ void store4(OutT *p, OutT a, OutT b, OutT c, OutT d);
+template <>
+__device__ __forceinline__ void store4<uint32_t>(uint32_t *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<float>(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double *p, double a, double b, double c, double d)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
+
+// Big offsets.
+__device__ __forceinline__ int u256_bit(const U256 &e, int b) { return (int)((e.w[b >> 6] >> (b & 63)) & 1u); }
+
+}  // namespace prand

@@ -1,0 +1,394 @@
+// MRG32K3A (Sec. 5.2) and LFSR113 (Sec. 5.3): seeding, jump tables, block
+// splitting, skip-ahead and multi-stream generation.
+//
+// Both generators keep their whole state in registers (6 and 4 words), so one
+// thread runs one section of one stream: sections of a stream start at
+// multiples of the section length, reached by the exact jump (A^n, B^n mod m;
+// GF(2) powers of the LFSR word step), exactly as the paper's array fill
+// splits an array into sections (Sec. 6).  State is stored structure-of-arrays
+// (word c of stream j at state[c * nstreams + j]) so a warp loads it coalesced.
+#include "devcommon.cuh"
+
+namespace prand {
+
+// =========================================================== MRG32K3A
+// Matrices of Sec. 5.2 with the negative entries taken mod m.
+__device__ __forceinline__ void mrg_step_matrices(uint32_t A[9], uint32_t B[9])
+{
+    const uint32_t a0[9] = { 0u, 1403580u, kM1 - 810728u, 1u, 0u, 0u, 0u, 1u, 0u };
+    const uint32_t b0[9] = { 527612u, 0u, kM2 - 1370589u, 1u, 0u, 0u, 0u, 1u, 0u };
+    for (int i = 0; i < 9; ++i) { A[i] = a0[i]; B[i] = b0[i]; }
+}
+
+template <uint32_t C>
+__device__ void mat3_sqr(uint32_t M[9])
+{
+    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
+    uint32_t R[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            uint32_t s = 0;
+            for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], M[3 * k + j]), m);
+            R[3 * i + j] = s;
+        }
+    for (int i = 0; i < 9; ++i) M[i] = R[i];
+}
+
+template <uint32_t C>
+__device__ __forceinline__ void mat3_vec(const uint32_t *M, uint32_t v[3])
+{
+    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
+    uint32_t r[3];
+    for (int i = 0; i < 3; ++i) {
+        uint32_t s = 0;
+        for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], v[k]), m);
+        r[i] = s;
+    }
+    v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
+}
+
+// tab[b] = (A^(2^b) mod m1, B^(2^b) mod m2), b < kJumpBits.
+__global__ void mrg_table_kernel(uint32_t *tab)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t A[9], B[9];
+    mrg_step_matrices(A, B);
+    for (int b = 0; b < kJumpBits; ++b) {
+        for (int i = 0; i < 9; ++i) { tab[18 * b + i] = A[i]; tab[18 * b + 9 + i] = B[i]; }
+        mat3_sqr<209>(A);
+        mat3_sqr<22853>(B);
+    }
+}
+
+// Apply the jump of bit b of the table to (x, y).
+__device__ __forceinline__ void mrg_apply_bit(const uint32_t *tab, int b, uint32_t x[3], uint32_t y[3])
+{
+    mat3_vec<209>(tab + 18 * b, x);
+    mat3_vec<22853>(tab + 18 * b + 9, y);
+}
+
+// Default state: all six words 12345 (the paper does not print it; L'Ecuyer's
+// package default).  Seeded: SplitMix64 draws, x mod m1, y mod m2, never all zero.
+__global__ void mrg_seed_kernel(uint32_t *base, uint64_t seed)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (seed == PRAND_SEED_DEFAULT) {
+        for (int i = 0; i < 6; ++i) base[i] = 12345u;
+        return;
+    }
+    uint64_t sm = seed;
+    uint32_t x[3], y[3];
+    do { for (int i = 0; i < 3; ++i) x[i] = (uint32_t)(splitmix64_next(sm) % kM1); } while (!(x[0] | x[1] | x[2]));
+    do { for (int i = 0; i < 3; ++i) y[i] = (uint32_t)(splitmix64_next(sm) % kM2); } while (!(y[0] | y[1] | y[2]));
+    for (int i = 0; i < 3; ++i) { base[i] = x[i]; base[3 + i] = y[i]; }
+}
+
+// Stream j = base advanced by (first + j) * 2^127.
+__global__ void mrg_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n)
+{
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t x[3] = { base[0], base[1], base[2] }, y[3] = { base[3], base[4], base[5] };
+    uint64_t k = first + j;
+    for (int b = 0; b < 64; ++b)
+        if ((k >> b) & 1u) mrg_apply_bit(tab, kMrgStreamShift + b, x, y);
+    for (int i = 0; i < 3; ++i) { state[i * n + j] = x[i]; state[(3 + i) * n + j] = y[i]; }
+}
+
+__global__ void mrg_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t n, U256 off)
+{
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t x[3], y[3];
+    for (int i = 0; i < 3; ++i) { x[i] = state[i * n + j]; y[i] = state[(3 + i) * n + j]; }
+    for (int b = 0; b < kJumpBits; ++b)
+        if (u256_bit(off, b)) mrg_apply_bit(tab, b, x, y);
+    for (int i = 0; i < 3; ++i) { state[i * n + j] = x[i]; state[(3 + i) * n + j] = y[i]; }
+}
+
+// One step of both components and the output z = (x - y) mod m1 in [1, m1].
+// x_{n+1} = 1403580 x_{n-1} - 810728 x_{n-2} (mod m1)
+// y_{n+1} = 527612 y_n - 1370589 y_{n-2}     (mod m2)
+__device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                             uint32_t &y0, uint32_t &y1, uint32_t &y2)
+{
+    // signed difference of two < 2^53 products, shifted positive by a multiple of m
+    uint64_t u = (uint64_t)1403580u * x1 + (uint64_t)810728u * (uint64_t)kM1 - (uint64_t)810728u * x2;  // < 2^54
+    uint64_t r = (u & 0xFFFFFFFFull) + 209ull * (u >> 32);                                                 // < 2^32 + 2^30
+    uint32_t xn = (uint32_t)(r >= kM1 ? r - kM1 : r);
+    uint64_t w = (uint64_t)527612u * y0 + (uint64_t)1370589u * (uint64_t)kM2 - (uint64_t)1370589u * y2;   // < 2^54
+    uint64_t s = (w & 0xFFFFFFFFull) + 22853ull * (w >> 32);                                               // < 2^32 + 2^37
+    s = (s & 0xFFFFFFFFull) + 22853ull * (s >> 32);                                                        // < 2^32 + 2^20
+    uint32_t yn = (uint32_t)(s >= kM2 ? s - kM2 : s);
+    x2 = x1; x1 = x0; x0 = xn;
+    y2 = y1; y1 = y0; y0 = yn;
+    return xn > yn ? xn - yn : xn - yn + kM1;
+}
+
+// One thread = one section of one stream.  Sections have length seclen (the
+// last one may be shorter); the thread of the last section writes the stream's
+// next state to sout, a separate buffer when a stream has several sections (so
+// no thread reads a state that another thread has already replaced).
+template <typename OutT>
+__global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
+                                                      uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                      OutT *__restrict__ out, int vec)
+{
+    uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nstreams * nsec) return;
+    uint64_t j = tid % nstreams;
+    uint32_t sec = (uint32_t)(tid / nstreams);
+    uint64_t start = (uint64_t)sec * seclen;
+    if (start >= nper) return;
+    uint64_t len = min(seclen, nper - start);
+    uint32_t x0 = state[j], x1 = state[nstreams + j], x2 = state[2 * nstreams + j];
+    uint32_t y0 = state[3 * nstreams + j], y1 = state[4 * nstreams + j], y2 = state[5 * nstreams + j];
+    if (start) {
+        uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
+        for (int b = 0; b < 64; ++b)
+            if ((start >> b) & 1u) mrg_apply_bit(tab, b, x, y);
+        x0 = x[0]; x1 = x[1]; x2 = x[2]; y0 = y[0]; y1 = y[1]; y2 = y[2];
+    }
+    OutT *o = out + j * nper + start;
+    uint64_t i = 0;
+    if (vec) {
+        for (; i < len && (((j * nper + start + i) & 3u) != 0); ++i) o[i] = Cvt<OutT, true>::f(mrg_next(x0, x1, x2, y0, y1, y2));
+        for (; i + 4 <= len; i += 4) {
+            uint32_t a = mrg_next(x0, x1, x2, y0, y1, y2), b = mrg_next(x0, x1, x2, y0, y1, y2);
+            uint32_t c = mrg_next(x0, x1, x2, y0, y1, y2), d = mrg_next(x0, x1, x2, y0, y1, y2);
+            store4<OutT>(o + i, Cvt<OutT, true>::f(a), Cvt<OutT, true>::f(b), Cvt<OutT, true>::f(c), Cvt<OutT, true>::f(d));
+        }
+    }
+    for (; i < len; ++i) o[i] = Cvt<OutT, true>::f(mrg_next(x0, x1, x2, y0, y1, y2));
+    if (start + len == nper) {
+        sout[j] = x0; sout[nstreams + j] = x1; sout[2 * nstreams + j] = x2;
+        sout[3 * nstreams + j] = y0; sout[4 * nstreams + j] = y1; sout[5 * nstreams + j] = y2;
+    }
+}
+
+// =========================================================== LFSR113
+// Component (p, q, s): (31,6,18), (29,2,2), (28,13,7), (25,3,13).  The word
+// holds bits x_{ns}..x_{ns+31} of eq. (lfsrOutput); a step keeps the top p bits
+// shifted by s and refills the rest through eq. (lfsrRel1).
+template <int P, int Q, int S>
+__host__ __device__ __forceinline__ uint32_t taus_step(uint32_t z)
+{
+    constexpr uint32_t mask = 0xFFFFFFFFu << (32 - P);
+    return ((z & mask) << S) ^ (((z << Q) ^ z) >> (P - S));
+}
+
+__device__ __forceinline__ uint32_t lfsr_comp_step(int c, uint32_t z)
+{
+    switch (c) {
+    case 0: return taus_step<31, 6, 18>(z);
+    case 1: return taus_step<29, 2, 2>(z);
+    case 2: return taus_step<28, 13, 7>(z);
+    default: return taus_step<25, 3, 13>(z);
+    }
+}
+
+__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *col, uint32_t v)
+{
+    uint32_t r = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) r ^= ((v >> i) & 1u) ? col[i] : 0u;
+    return r;
+}
+
+// tab[(c * kJumpBits + b) * 32 + i] = image of bit i under the word step of
+// component c applied 2^b times.  One thread per component.
+__global__ void lfsr_table_kernel(uint32_t *tab)
+{
+    int c = threadIdx.x;
+    if (c >= 4 || blockIdx.x != 0) return;
+    uint32_t col[32], sq[32];
+    for (int i = 0; i < 32; ++i) col[i] = lfsr_comp_step(c, 1u << i);
+    for (int b = 0; b < kJumpBits; ++b) {
+        for (int i = 0; i < 32; ++i) tab[((size_t)c * kJumpBits + b) * 32 + i] = col[i];
+        for (int i = 0; i < 32; ++i) sq[i] = gf2_apply(col, col[i]);
+        for (int i = 0; i < 32; ++i) col[i] = sq[i];
+    }
+}
+
+__device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint32_t z[4])
+{
+    for (int c = 0; c < 4; ++c) z[c] = gf2_apply(tab + ((size_t)c * kJumpBits + b) * 32, z[c]);
+}
+
+// Default state: 987654321 in all four words (L'Ecuyer's example seed; the paper
+// prints none).  Seeded: the high 32 bits of SplitMix64 draws, redrawn while
+// the top p bits of a component are all zero.
+__global__ void lfsr_seed_kernel(uint32_t *base, uint64_t seed)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int P[4] = { 31, 29, 28, 25 };
+    if (seed == PRAND_SEED_DEFAULT) {
+        for (int c = 0; c < 4; ++c) base[c] = 987654321u;
+        return;
+    }
+    uint64_t sm = seed;
+    for (int c = 0; c < 4; ++c) {
+        uint32_t w;
+        do { w = (uint32_t)(splitmix64_next(sm) >> 32); } while ((w >> (32 - P[c])) == 0u);
+        base[c] = w;
+    }
+}
+
+__global__ void lfsr_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n)
+{
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t z[4] = { base[0], base[1], base[2], base[3] };
+    uint64_t k = first + j;
+    for (int b = 0; b < 64; ++b)
+        if ((k >> b) & 1u) lfsr_apply_bit(tab, kLfsrStreamShift + b, z);
+    for (int c = 0; c < 4; ++c) state[c * n + j] = z[c];
+}
+
+__global__ void lfsr_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t n, U256 off)
+{
+    uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t z[4];
+    for (int c = 0; c < 4; ++c) z[c] = state[c * n + j];
+    for (int b = 0; b < kJumpBits; ++b)
+        if (u256_bit(off, b)) lfsr_apply_bit(tab, b, z);
+    for (int c = 0; c < 4; ++c) state[c * n + j] = z[c];
+}
+
+__device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)
+{
+    z0 = taus_step<31, 6, 18>(z0);
+    z1 = taus_step<29, 2, 2>(z1);
+    z2 = taus_step<28, 13, 7>(z2);
+    z3 = taus_step<25, 3, 13>(z3);
+    return z0 ^ z1 ^ z2 ^ z3;
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
+                                                       uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                       OutT *__restrict__ out, int vec)
+{
+    uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nstreams * nsec) return;
+    uint64_t j = tid % nstreams;
+    uint32_t sec = (uint32_t)(tid / nstreams);
+    uint64_t start = (uint64_t)sec * seclen;
+    if (start >= nper) return;
+    uint64_t len = min(seclen, nper - start);
+    uint32_t z0 = state[j], z1 = state[nstreams + j], z2 = state[2 * nstreams + j], z3 = state[3 * nstreams + j];
+    if (start) {
+        uint32_t z[4] = { z0, z1, z2, z3 };
+        for (int b = 0; b < 64; ++b)
+            if ((start >> b) & 1u) lfsr_apply_bit(tab, b, z);
+        z0 = z[0]; z1 = z[1]; z2 = z[2]; z3 = z[3];
+    }
+    OutT *o = out + j * nper + start;
+    uint64_t i = 0;
+    if (vec) {
+        for (; i < len && (((j * nper + start + i) & 3u) != 0); ++i) o[i] = Cvt<OutT>::f(lfsr_next(z0, z1, z2, z3));
+        for (; i + 4 <= len; i += 4) {
+            uint32_t a = lfsr_next(z0, z1, z2, z3), b = lfsr_next(z0, z1, z2, z3);
+            uint32_t c = lfsr_next(z0, z1, z2, z3), d = lfsr_next(z0, z1, z2, z3);
+            store4<OutT>(o + i, Cvt<OutT>::f(a), Cvt<OutT>::f(b), Cvt<OutT>::f(c), Cvt<OutT>::f(d));
+        }
+    }
+    for (; i < len; ++i) o[i] = Cvt<OutT>::f(lfsr_next(z0, z1, z2, z3));
+    if (start + len == nper) {
+        sout[j] = z0; sout[nstreams + j] = z1; sout[2 * nstreams + j] = z2; sout[3 * nstreams + j] = z3;
+    }
+}
+
+// =========================================================== host launchers
+static unsigned grid_for(uint64_t n, unsigned block) { return (unsigned)((n + block - 1) / block); }
+
+prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st)
+{
+    mrg_table_kernel<<<1, 32, 0, st>>>(tab);
+    return launch_check();
+}
+
+prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st)
+{
+    lfsr_table_kernel<<<1, 32, 0, st>>>(tab);
+    return launch_check();
+}
+
+prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st)
+{
+    if (gen == PRAND_MRG32K3A) mrg_seed_kernel<<<1, 32, 0, st>>>((uint32_t *)d_base, seed);
+    else lfsr_seed_kernel<<<1, 32, 0, st>>>((uint32_t *)d_base, seed);
+    return launch_check();
+}
+
+prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                             cudaStream_t st)
+{
+    const unsigned B = 128;
+    if (gen == PRAND_MRG32K3A)
+        mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+    else
+        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+    return launch_check();
+}
+
+prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st)
+{
+    const unsigned B = 128;
+    if (gen == PRAND_MRG32K3A) mrg_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (uint32_t *)d_state, n, off);
+    else lfsr_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (uint32_t *)d_state, n, off);
+    return launch_check();
+}
+
+// Sections per stream: enough threads to fill the GPU (about 8 resident warps
+// of work per SM scheduler), sections no shorter than 256 outputs.
+static void pick_sections(uint64_t nstreams, uint64_t nper, uint32_t *nsec, uint64_t *seclen)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t target = (uint64_t)sms * 2048;
+    uint64_t s = 1;
+    if (nstreams < target) s = (target + nstreams - 1) / nstreams;
+    uint64_t maxs = nper / 256 ? nper / 256 : 1;
+    if (s > maxs) s = maxs;
+    if (s > 65535) s = 65535;
+    uint64_t len = (nper + s - 1) / s;
+    len = (len + 3) & ~3ull;  // keep section starts 4-aligned for vector stores
+    if (len == 0) len = 4;
+    *seclen = len;
+    *nsec = (uint32_t)((nper + len - 1) / len);
+    if (*nsec == 0) *nsec = 1;
+}
+
+template <typename OutT>
+static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams,
+                                     OutT *out, uint64_t nper, cudaStream_t st, bool *swapped)
+{
+    uint32_t nsec;
+    uint64_t seclen;
+    pick_sections(nstreams, nper, &nsec, &seclen);
+    int vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0;
+    const unsigned B = 256;
+    uint64_t threads = nstreams * nsec;
+    uint32_t *sin = (uint32_t *)d_state, *sout = nsec > 1 ? (uint32_t *)d_spare : sin;
+    *swapped = nsec > 1;
+    if (gen == PRAND_MRG32K3A)
+        mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+    else
+        lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+    return launch_check();
+}
+
+prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
+                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped)
+{
+    if (dtype == PRAND_DTYPE_U32)
+        return mrg_lfsr_gen_t<uint32_t>(gen, T, d_state, d_spare, nstreams, (uint32_t *)out, nper, st, swapped);
+    if (dtype == PRAND_DTYPE_F32)
+        return mrg_lfsr_gen_t<float>(gen, T, d_state, d_spare, nstreams, (float *)out, nper, st, swapped);
+    return mrg_lfsr_gen_t<double>(gen, T, d_state, d_spare, nstreams, (double *)out, nper, st, swapped);
+}
+
+}  // namespace prand

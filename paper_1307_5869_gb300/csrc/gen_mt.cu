@@ -1,0 +1,305 @@
+// MT19937 (Matsumoto & Nishimura 1998; Sec. 5.4): seeding, warp-cooperative
+// generation and the polynomial jump-ahead of eq. (g_v).
+//
+// One warp owns one stream.  The 624-word state lives in shared memory and is
+// twisted by the 32 lanes in the three dependency phases of the recurrence
+// x_{t+624} = x_{t+397} ^ twist(x_t^u | x_{t+1}^l): words 0..226 read only old
+// words, words 227..453 read words 0..226 of the new block, words 454..623 read
+// words 227..396 of the new block (Table 5 uses 227 threads per stream for the
+// same reason).  Output words leave tempered, 32 consecutive words per store
+// instruction.
+//
+// State layout: stream j at state[j * 624 .. j * 624 + 623].  All streams of a
+// handle share the position inside the current block (the handle's index), so
+// the index is kept on the host.
+//
+// Jump (Sec. 5.4): A^v Y = g_v(A) Y = sum_i a_i A^(i-1) Y with g_v = x^v mod phi.
+// With Y in window form (x_t..x_{t+623}), A^i Y is the window starting at
+// x_{t+i}, so the sum is a sliding-window XOR over the stream's next 20560
+// words, taken at the set coefficients of g_v.
+#include "devcommon.cuh"
+
+namespace prand {
+
+constexpr int kMtWarpsPerBlock = 4;
+
+__device__ __forceinline__ uint32_t mt_recur(uint32_t xt, uint32_t xt1, uint32_t xt397)
+{
+    uint32_t y = (xt & 0x80000000u) | (xt1 & 0x7FFFFFFFu);
+    return xt397 ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
+}
+
+__device__ __forceinline__ uint32_t mt_temper(uint32_t y)
+{
+    y ^= y >> 11;
+    y ^= (y << 7) & 0x9D2C5680u;
+    y ^= (y << 15) & 0xEFC60000u;
+    y ^= y >> 18;
+    return y;
+}
+
+// ------------------------------------------------------------------ seeding
+// seed < 2^32: init_genrand(seed); wider seeds: init_by_array({lo32, hi32});
+// PRAND_SEED_DEFAULT: init_genrand(5489).  One thread (the recurrence is serial).
+__global__ void mt_seed_kernel(uint32_t *base, uint64_t seed)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    auto genrand_init = [&](uint32_t s) {
+        base[0] = s;
+        for (uint32_t i = 1; i < kMtN; ++i) base[i] = 1812433253u * (base[i - 1] ^ (base[i - 1] >> 30)) + i;
+    };
+    if (seed == PRAND_SEED_DEFAULT) { genrand_init(5489u); return; }
+    if (seed <= 0xFFFFFFFFull) { genrand_init((uint32_t)seed); return; }
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    genrand_init(19650218u);
+    int i = 1, j = 0;
+    for (int k = kMtN; k; --k) {
+        base[i] = (base[i] ^ ((base[i - 1] ^ (base[i - 1] >> 30)) * 1664525u)) + key[j] + (uint32_t)j;
+        ++i; ++j;
+        if (i >= kMtN) { base[0] = base[kMtN - 1]; i = 1; }
+        if (j >= 2) j = 0;
+    }
+    for (int k = kMtN - 1; k; --k) {
+        base[i] = (base[i] ^ ((base[i - 1] ^ (base[i - 1] >> 30)) * 1566083941u)) - (uint32_t)i;
+        ++i;
+        if (i >= kMtN) { base[0] = base[kMtN - 1]; i = 1; }
+    }
+    base[0] = 0x80000000u;
+}
+
+// ------------------------------------------------------------------ twist
+// In-place twist of a 624-word block in shared memory by one warp.
+__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane)
+{
+    // phase 1: k in [0, 227) reads mt[k+397] (old)
+    // phase 2: k in [227, 454) reads mt[k-227] (new, phase 1)
+    // phase 3: k in [454, 624) reads mt[k-227] (new, phase 2); k = 623 reads mt[0] (new)
+    const int lo[3] = { 0, 227, 454 }, hi[3] = { 227, 454, 624 };
+#pragma unroll
+    for (int ph = 0; ph < 3; ++ph) {
+        for (int k0 = lo[ph]; k0 < hi[ph]; k0 += 32) {
+            int k = k0 + lane;
+            bool act = k < hi[ph];
+            uint32_t a = 0, b = 0, c = 0;
+            if (act) {
+                a = mt[k];
+                b = mt[k + 1 < kMtN ? k + 1 : 0];
+                c = mt[k < 227 ? k + 397 : k - 227];
+            }
+            __syncwarp();
+            if (act) mt[k] = mt_recur(a, b, c);
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ generation
+template <typename OutT>
+__global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_gen_kernel(uint32_t *state, uint64_t nstreams, uint32_t idx0,
+                                                                       uint64_t nper, OutT *__restrict__ out)
+{
+    __shared__ uint32_t sm[kMtWarpsPerBlock][kMtN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
+    if (j >= nstreams) return;  // whole warp
+    uint32_t *mt = sm[w];
+    const uint32_t *src = state + j * kMtN;
+    for (int i = lane; i < kMtN; i += 32) mt[i] = src[i];
+    __syncwarp();
+    uint32_t idx = idx0;
+    uint64_t done = 0;
+    OutT *o = out + j * nper;
+    while (done < nper) {
+        if (idx >= (uint32_t)kMtN) { mt_twist_warp(mt, lane); idx = 0; }
+        uint64_t cnt = min((uint64_t)(kMtN - idx), nper - done);
+        for (uint64_t t = lane; t < cnt; t += 32) o[done + t] = Cvt<OutT>::f(mt_temper(mt[idx + t]));
+        idx += (uint32_t)cnt;
+        done += cnt;
+    }
+    __syncwarp();
+    uint32_t *dst = state + j * kMtN;
+    for (int i = lane; i < kMtN; i += 32) dst[i] = mt[i];
+}
+
+// ------------------------------------------------------------------ jump
+// dst := g(A) src for one stream, by one warp.  seq is a 1248-word ring in
+// shared memory holding two consecutive 624-word blocks of the stream.
+// acc[r] accumulates result word m = lane + 32 r (m < 624).
+__device__ void mt_apply_poly_warp(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst, uint32_t *seq,
+                                   int lane)
+{
+    constexpr int R = (kMtN + 31) / 32;  // 20
+    uint32_t acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    for (int i = lane; i < kMtN; i += 32) seq[i] = src[i];
+    __syncwarp();
+    // block 1 = words 624..1247 of the stream, into slot 1
+    auto twist_into = [&](int out_slot) {
+        // x_T = recur(x_{T-624}, x_{T-623}, x_{T-227}) for T in the new block;
+        // the previous block sits in the other slot.
+        uint32_t *nb = seq + out_slot * kMtN;
+        const uint32_t *ob = seq + (out_slot ^ 1) * kMtN;
+        const int lo[3] = { 0, 227, 454 }, hi[3] = { 227, 454, 624 };
+#pragma unroll
+        for (int ph = 0; ph < 3; ++ph) {
+            for (int k = lo[ph] + lane; k < hi[ph]; k += 32) {
+                uint32_t a = ob[k];
+                uint32_t b = (k + 1 < kMtN) ? ob[k + 1] : nb[0];
+                uint32_t c = (k < 227) ? ob[k + 397] : nb[k - 227];
+                nb[k] = mt_recur(a, b, c);
+            }
+            __syncwarp();
+        }
+    };
+    twist_into(1);
+    // coefficient i of g (i < 19937) selects the window starting at x_i.
+    for (int B = 0; B * kMtN < kMtDeg; ++B) {
+        const int base_slot = B & 1;
+        const int i_lo = B * kMtN, i_hi = min(i_lo + kMtN, kMtDeg);
+        for (int wd = i_lo >> 5; (wd << 5) < i_hi; ++wd) {
+            uint32_t bits = __ldg(poly + wd);
+            // keep the bits of this word that fall in [i_lo, i_hi)
+            int b0 = (wd << 5);
+            if (b0 < i_lo) bits &= 0xFFFFFFFFu << (i_lo - b0);
+            if (b0 + 32 > i_hi) bits &= (i_hi - b0) >= 32 ? 0xFFFFFFFFu : ((1u << (i_hi - b0)) - 1u);
+            while (bits) {
+                int bb = __ffs(bits) - 1;
+                bits &= bits - 1;
+                int d = b0 + bb - i_lo;                  // offset of x_i inside block B
+                int p0 = base_slot * kMtN + d;           // ring position of x_i
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int m = lane + 32 * r;
+                    if (m < kMtN) {
+                        int p = p0 + m;
+                        if (p >= 2 * kMtN) p -= 2 * kMtN;
+                        acc[r] ^= seq[p];
+                    }
+                }
+            }
+        }
+        // the window of the next block needs block B + 2 in slot (B & 1)
+        if ((B + 1) * kMtN < kMtDeg) {
+            __syncwarp();
+            twist_into(base_slot);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int m = lane + 32 * r;
+        if (m < kMtN) dst[m] = acc[r];
+    }
+}
+
+// Doubling level: dst stream (off + j) := g(A) (src stream j), j < count.
+__global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_level_kernel(const uint32_t *poly, uint32_t *state,
+                                                                         uint64_t off, uint64_t count)
+{
+    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
+    if (j >= count) return;
+    mt_apply_poly_warp(poly, state + j * kMtN, state + (off + j) * kMtN, seq[w], lane);
+}
+
+// Every stream advanced by the set bits of a 512-bit offset (one polynomial
+// x^(2^b) mod phi per set bit b, applied one after another in place).
+struct MtBits { uint64_t w[8]; };
+
+__global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_multi_kernel(const uint32_t *polys, uint32_t *state,
+                                                                         uint64_t n, MtBits e, uint32_t *scratch)
+{
+    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
+    if (j >= n) return;
+    uint32_t *s = state + j * kMtN;
+    for (int b = 0; b < 512; ++b) {
+        if (!((e.w[b >> 6] >> (b & 63)) & 1u)) continue;
+        // result goes to registers then back over s (src is copied to smem first)
+        mt_apply_poly_warp(polys + (size_t)b * kMtPolyWords, s, s, seq[w], lane);
+        __syncwarp();
+    }
+    (void)scratch;
+}
+
+// ------------------------------------------------------------------ host
+static unsigned grid_warps(uint64_t n) { return (unsigned)((n + kMtWarpsPerBlock - 1) / kMtWarpsPerBlock); }
+
+prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st)
+{
+    mt_seed_kernel<<<1, 32, 0, st>>>((uint32_t *)d_base, seed);
+    return launch_check();
+}
+
+// streams j = 0..n-1 := base advanced by (first + j) * 2^432: stream 0 by the
+// bits of first, then a doubling tree (stream 2^b + j from stream j by 2^(432+b)).
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st)
+{
+    uint32_t *state = (uint32_t *)d_state;
+    if (cudaMemcpyAsync(state, d_base, kMtN * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return PRAND_ERR_CUDA;
+    if (first) {
+        MtBits e = {};
+        // first * 2^432: bits 432 .. 495
+        for (int b = 0; b < 64; ++b)
+            if ((first >> b) & 1u) e.w[(kMtStreamShift + b) >> 6] |= 1ull << ((kMtStreamShift + b) & 63);
+        mt_multi_kernel<<<1, 32 * kMtWarpsPerBlock, 0, st>>>(T->mt, state, 1, e, nullptr);
+        prand_status_t s = launch_check();
+        if (s != PRAND_OK) return s;
+    }
+    for (int b = 0; b < 64 && (1ull << b) < n; ++b) {
+        uint64_t have = 1ull << b;
+        uint64_t count = min(have, n - have);
+        mt_level_kernel<<<grid_warps(count), 32 * kMtWarpsPerBlock, 0, st>>>(
+            T->mt + (size_t)(kMtStreamShift + b) * kMtPolyWords, state, have, count);
+        prand_status_t s = launch_check();
+        if (s != PRAND_OK) return s;
+    }
+    return PRAND_OK;
+}
+
+// Skip ahead: consume the rest of the current block, then jump by polynomials.
+prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off_in, cudaStream_t st)
+{
+    U256 off = off_in;
+    if (*idx < (uint32_t)kMtN) {
+        uint64_t rem = kMtN - *idx;
+        bool small = !off.w[1] && !off.w[2] && !off.w[3];
+        if (small && off.w[0] < rem) { *idx += (uint32_t)off.w[0]; return PRAND_OK; }
+        uint64_t borrow = rem;
+        for (int i = 0; i < 4 && borrow; ++i) {
+            uint64_t before = off.w[i];
+            off.w[i] -= borrow;
+            borrow = before < borrow ? 1 : 0;
+        }
+        *idx = kMtN;
+    }
+    MtBits e = {};
+    for (int i = 0; i < 4; ++i) e.w[i] = off.w[i];
+    bool any = false;
+    for (int i = 0; i < 4; ++i) any = any || e.w[i];
+    if (!any) return PRAND_OK;
+    mt_multi_kernel<<<grid_warps(n), 32 * kMtWarpsPerBlock, 0, st>>>(T->mt, (uint32_t *)d_state, n, e, nullptr);
+    return launch_check();
+}
+
+prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st)
+{
+    uint32_t *state = (uint32_t *)d_state;
+    unsigned grid = grid_warps(nstreams);
+    if (dtype == PRAND_DTYPE_U32) mt_gen_kernel<uint32_t><<<grid, 32 * kMtWarpsPerBlock, 0, st>>>(state, nstreams, *idx, nper, (uint32_t *)out);
+    else if (dtype == PRAND_DTYPE_F32) mt_gen_kernel<float><<<grid, 32 * kMtWarpsPerBlock, 0, st>>>(state, nstreams, *idx, nper, (float *)out);
+    else mt_gen_kernel<double><<<grid, 32 * kMtWarpsPerBlock, 0, st>>>(state, nstreams, *idx, nper, (double *)out);
+    prand_status_t s = launch_check();
+    if (s != PRAND_OK) return s;
+    // the index after nper outputs: the rest of the current block, then whole blocks
+    uint64_t avail = kMtN - *idx;
+    if (nper <= avail) *idx += (uint32_t)nper;
+    else *idx = (uint32_t)((nper - avail - 1) % kMtN + 1);
+    return PRAND_OK;
+}
+
+}  // namespace prand

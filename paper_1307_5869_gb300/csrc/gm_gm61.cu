@@ -1,0 +1,6 @@
+// GM61 instantiation of the torus-map ensemble kernels (see gm_impl.cuh).
+#include "gm_impl.cuh"
+
+namespace prand {
+PRAND_GM_INSTANTIATE(PRAND_GM61, gm61)
+}  // namespace prand

@@ -1,0 +1,389 @@
+// GM19, GM29, GM31, GM55, GM61, GQ58.1, GQ58.3, GQ58.4: ensembles of s
+// two-dimensional torus maps x^(n) = k x^(n-1) - q x^(n-2) (mod g) (Sec. 5.1,
+// eq. (rec1), parameters of Table 2).
+//
+// GPU layout: a group of `lanes` consecutive lanes (32, 8 or 16) runs one
+// stream, one torus point per lane, so every lane does exactly one recurrence
+// step per output word.  The word is assembled across the group with a warp
+// ballot (v = 1) or a shuffle-OR tree (v = 3, 4); the group then hands word t
+// to lane (t / 4) mod lanes, which emits four words at a time as one 16-byte
+// store, so each group writes 16 * lanes contiguous bytes per round.
+//
+// Arithmetic is exact in 64-bit integers on z = x / 2^t modulo the prime p
+// (g = 2^t p; for GM55 and GQ58.x, k and q are even, so states kept on
+// multiples of 2^t stay there and z follows the same recurrence mod p).
+// The state is stored as x = 2^t z, (x^(n-1), x^(n)) per point.
+//
+// Readings (the paper prints only k, q, g, v): s = 32 points for v = 1, 8 for
+// v = 4, 12 for GQ58.3 (Table 5's threads per section); point i contributes
+// floor(2^v x_i / g) at bit v*i (truncated to 32 bits); point i of the base
+// ensemble is the base pair advanced by i * D, D = nmax * L (Table 4).
+#pragma once
+#include "devcommon.cuh"
+
+namespace prand {
+
+template <int GEN>
+struct GmT;
+// k, q, p, t, v, s, lanes, prime kind, L, nmax
+#define PRAND_GM_TRAITS(GEN, K, Q, PP, T, V, S, LANES, KIND, L, NMAX)                                   \
+    template <>                                                                                       \
+    struct GmT<GEN> {                                                                                 \
+        static constexpr uint64_t k = K, q = Q, p = PP, L_ = L, nmax = NMAX;                            \
+        static constexpr int t = T, v = V, s = S, lanes = LANES, kind = KIND;                          \
+    };
+PRAND_GM_TRAITS(PRAND_GM19, 15, 28, (1ull << 19) - 1, 0, 1, 32, 32, P19, 6000000ull, 1000ull)
+PRAND_GM_TRAITS(PRAND_GM29, 4, 2, (1ull << 29) - 3, 0, 1, 32, 32, P29, 80000000ull, 100000000ull)
+PRAND_GM_TRAITS(PRAND_GM31, 11, 14, (1ull << 31) - 1, 0, 1, 32, 32, P31, 80000000ull, 1000000000ull)
+PRAND_GM_TRAITS(PRAND_GM55, 256, 176, (1ull << 51) - 129, 4, 4, 8, 8, P51, 10000000000ull, 1000000000000000000ull)
+PRAND_GM_TRAITS(PRAND_GM61, 24, 74, (1ull << 61) - 1, 0, 1, 32, 32, P61, 10000000000ull, 18000000000000000000ull)
+PRAND_GM_TRAITS(PRAND_GQ58_1, 8, 48, (1ull << 29) - 3, 29, 1, 32, 32, P29, 80000000ull, 100000000ull)
+PRAND_GM_TRAITS(PRAND_GQ58_3, 8, 48, (1ull << 29) - 3, 29, 3, 12, 16, P29, 80000000ull, 200000000ull)
+PRAND_GM_TRAITS(PRAND_GQ58_4, 8, 48, (1ull << 29) - 3, 29, 4, 8, 8, P29, 80000000ull, 300000000ull)
+#undef PRAND_GM_TRAITS
+
+// ----------------------------------------------------------------- one step
+// z' = k z - q z_prev (mod p), computed as k z + q (p - z_prev) and folded.
+template <int GEN>
+__device__ __forceinline__ uint64_t gm_step(uint64_t zc, uint64_t zp);
+
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM19>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint32_t p = (1u << 19) - 1;
+    uint32_t s = 15u * (uint32_t)zc + 28u * (p - (uint32_t)zp);  // < 43 * 2^19
+    s = (s & p) + (s >> 19);                                    // < 2^19 + 43
+    return s >= p ? s - p : s;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM29>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint32_t p = (1u << 29) - 3, m = (1u << 29) - 1;
+    uint32_t s = 4u * (uint32_t)zc + 2u * (p - (uint32_t)zp);   // < 6 * 2^29 < 2^32
+    s = (s & m) + 3u * (s >> 29);                               // < 2^29 + 18
+    return s >= p ? s - p : s;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM31>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint64_t p = (1ull << 31) - 1;
+    uint64_t s = 11ull * zc + 14ull * (p - zp);                  // < 25 * 2^31
+    s = (s & p) + (s >> 31);                                     // < 2^31 + 25
+    return s >= p ? s - p : s;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint64_t p = (1ull << 51) - 129, m = (1ull << 51) - 1;
+    uint64_t s = (zc << 8) + 176ull * (p - zp);                  // < 432 * 2^51 < 2^60
+    s = (s & m) + 129ull * (s >> 51);                            // < 2^51 + 2^16
+    return s >= p ? s - p : s;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM61>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint64_t p = (1ull << 61) - 1;
+    // 24 zc + 74 (p - zp) < 98 * 2^61: a 68-bit sum kept as (hi, lo)
+    uint64_t a_lo = zc * 24ull, a_hi = __umul64hi(zc, 24ull);
+    uint64_t y = p - zp;
+    uint64_t b_lo = y * 74ull, b_hi = __umul64hi(y, 74ull);
+    uint64_t lo = a_lo + b_lo;
+    uint64_t hi = a_hi + b_hi + (lo < a_lo ? 1ull : 0ull);
+    uint64_t r = (lo & p) + ((hi << 3) | (lo >> 61));            // < 2^61 + 2^11
+    return r >= p ? r - p : r;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_1>(uint64_t zc, uint64_t zp)
+{
+    constexpr uint64_t p = (1ull << 29) - 3, m = (1ull << 29) - 1;
+    uint64_t s = 8ull * zc + 48ull * (p - zp);                   // < 56 * 2^29
+    s = (s & m) + 3ull * (s >> 29);                              // < 2^29 + 168
+    return s >= p ? s - p : s;
+}
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_3>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_4>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
+
+// ----------------------------------------------------------------- strips
+// floor(2^v z / p) = floor(2^v x / g): the horizontal strip of the torus.
+template <int GEN>
+__device__ __forceinline__ uint32_t gm_strip(uint64_t z)
+{
+    using P = GmT<GEN>;
+    if (P::v == 1) return z > (P::p >> 1) ? 1u : 0u;  // p odd: 2z >= p  <=>  z > (p-1)/2
+    // p = 2^b - c: q0 = floor(2^v z / 2^b) <= answer <= q0 + 1
+    constexpr int b = P::kind == P51 ? 51 : 29;
+    constexpr uint64_t c = P::kind == P51 ? 129 : 3;
+    constexpr uint64_t m = (1ull << b) - 1;
+    uint64_t q0 = z >> (b - P::v);
+    uint64_t r = ((z << P::v) & m) + c * q0;  // 2^v z - q0 p
+    return (uint32_t)(q0 + (r >= P::p ? 1u : 0u));
+}
+
+// ----------------------------------------------------------------- jumps
+// M = [[k, -q], [1, 0]] acting on (z^(n), z^(n-1)); tab[b] = M^(2^b) mod p.
+template <int GEN>
+__global__ void gm_table_kernel(uint64_t *tab)
+{
+    using P = GmT<GEN>;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t m0 = P::k % P::p, m1 = P::p - P::q % P::p, m2 = 1, m3 = 0;
+#pragma unroll 1
+    for (int b = 0; b < kJumpBits; ++b) {
+        tab[4 * b] = m0; tab[4 * b + 1] = m1; tab[4 * b + 2] = m2; tab[4 * b + 3] = m3;
+        uint64_t n0 = addmod_p<P::kind>(mulmod_p<P::kind>(m0, m0), mulmod_p<P::kind>(m1, m2));
+        uint64_t n1 = addmod_p<P::kind>(mulmod_p<P::kind>(m0, m1), mulmod_p<P::kind>(m1, m3));
+        uint64_t n2 = addmod_p<P::kind>(mulmod_p<P::kind>(m2, m0), mulmod_p<P::kind>(m3, m2));
+        uint64_t n3 = addmod_p<P::kind>(mulmod_p<P::kind>(m2, m1), mulmod_p<P::kind>(m3, m3));
+        m0 = n0; m1 = n1; m2 = n2; m3 = n3;
+    }
+}
+
+template <int GEN>
+__device__ __forceinline__ void gm_apply(const uint64_t *M, uint64_t &zc, uint64_t &zp)
+{
+    using P = GmT<GEN>;
+    uint64_t c = addmod_p<P::kind>(mulmod_p<P::kind>(M[0], zc), mulmod_p<P::kind>(M[1], zp));
+    uint64_t q = addmod_p<P::kind>(mulmod_p<P::kind>(M[2], zc), mulmod_p<P::kind>(M[3], zp));
+    zc = c; zp = q;
+}
+
+// Jump by the 128-bit exponent (hi, lo).
+template <int GEN>
+__device__ __forceinline__ void gm_jump128(const uint64_t *tab, uint64_t lo, uint64_t hi, uint64_t &zc, uint64_t &zp)
+{
+#pragma unroll 1
+    for (int b = 0; b < 64; ++b)
+        if ((lo >> b) & 1u) gm_apply<GEN>(tab + 4 * b, zc, zp);
+#pragma unroll 1
+    for (int b = 0; b < 64; ++b)
+        if ((hi >> b) & 1u) gm_apply<GEN>(tab + 4 * (64 + b), zc, zp);
+}
+
+__device__ __forceinline__ void mul64x64(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
+{
+    lo = a * b;
+    hi = __umul64hi(a, b);
+}
+
+// Base ensemble: lane i < s gets the base pair advanced by i * D.
+template <int GEN>
+__global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t seed)
+{
+    using P = GmT<GEN>;
+    int i = threadIdx.x;
+    if (blockIdx.x != 0 || i >= P::s) return;
+    uint64_t a = 1, b = 1;
+    if (seed != PRAND_SEED_DEFAULT) {
+        uint64_t sm = seed;
+        do { a = splitmix64_next(sm) % P::p; b = splitmix64_next(sm) % P::p; } while (!(a | b));
+    }
+    uint64_t zp = a, zc = b;  // (z^(0), z^(1))
+    // e = i * nmax * L, as a 128-bit product (nmax * L < 2^98, i < 32)
+    uint64_t dlo, dhi;
+    mul64x64(P::nmax, P::L_, dlo, dhi);
+    uint64_t elo, ehi;
+    mul64x64(dlo, (uint64_t)i, elo, ehi);
+    ehi += dhi * (uint64_t)i;
+    gm_jump128<GEN>(tab, elo, ehi, zc, zp);
+    base[i] = zp << P::t;          // x^(n-1)
+    base[P::s + i] = zc << P::t;   // x^(n)
+}
+
+// Stream j of the handle = base advanced by (first + j) * L.  One group per stream.
+template <int GEN>
+__global__ void gm_init_kernel(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n)
+{
+    using P = GmT<GEN>;
+    uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / P::lanes;
+    int i = threadIdx.x % P::lanes;
+    if (g >= n || i >= P::s) return;
+    uint64_t zp = base[i] >> P::t, zc = base[P::s + i] >> P::t;
+    uint64_t elo, ehi;
+    mul64x64(first + g, P::L_, elo, ehi);
+    gm_jump128<GEN>(tab, elo, ehi, zc, zp);
+    state[g * P::s + i] = zp << P::t;
+    state[(n + g) * P::s + i] = zc << P::t;
+}
+
+template <int GEN>
+__global__ void gm_skip_kernel(const uint64_t *tab, uint64_t *state, uint64_t n, U256 off)
+{
+    using P = GmT<GEN>;
+    uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / P::lanes;
+    int i = threadIdx.x % P::lanes;
+    if (g >= n || i >= P::s) return;
+    uint64_t zp = state[g * P::s + i] >> P::t, zc = state[(n + g) * P::s + i] >> P::t;
+#pragma unroll 1
+    for (int b = 0; b < kJumpBits; ++b)
+        if (u256_bit(off, b)) gm_apply<GEN>(tab + 4 * b, zc, zp);
+    state[g * P::s + i] = zp << P::t;
+    state[(n + g) * P::s + i] = zc << P::t;
+}
+
+// ----------------------------------------------------------------- generation
+// OR-combine the word over the group (all lanes of the group end with it).
+template <int GEN>
+__device__ __forceinline__ uint32_t gm_word(uint32_t strip, int li, unsigned gmask)
+{
+    using P = GmT<GEN>;
+    if (P::v == 1) return __ballot_sync(gmask, strip);  // lanes == 32: lane i <-> bit i
+    uint32_t w = (li < P::s && P::v * li < 32) ? (strip << (P::v * li)) : 0u;
+#pragma unroll
+    for (int d = 1; d < P::lanes; d <<= 1) w |= __shfl_xor_sync(gmask, w, d);
+    return w;
+}
+
+// One group = one section of one stream.  A round makes up to 4 * lanes words;
+// lane li keeps words 4 li .. 4 li + 3 of the round and stores them together.
+// Every point takes exactly `len` steps, so the group of the last section holds
+// the stream's next state and writes it to state_out (a separate buffer when a
+// stream is split into several sections, so no group reads a state another
+// group has already replaced).
+template <int GEN, typename OutT>
+__global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
+                                                     uint64_t *state_out, uint64_t nstreams, uint64_t nper,
+                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out, int vec)
+{
+    using P = GmT<GEN>;
+    constexpr int G = P::lanes;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int li = threadIdx.x % G;
+    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1)));
+    if (gid >= nstreams * nsec) return;  // gid is uniform within a group
+    const uint64_t j = gid % nstreams;
+    const uint64_t start = (gid / nstreams) * seclen;
+    if (start >= nper) return;
+    const uint64_t len = min(seclen, nper - start);
+    const bool pt = li < P::s;
+    uint64_t zp = 0, zc = 0;
+    if (pt) {
+        zp = state_in[j * P::s + li] >> P::t;
+        zc = state_in[(nstreams + j) * P::s + li] >> P::t;
+        if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
+    }
+    OutT *o = out + j * nper + start;
+    const bool vgroup = vec && (((j * nper + start) & 3u) == 0);
+    for (uint64_t base = 0; base < len; base += 4 * G) {
+        const uint64_t rem = len - base;
+        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+#pragma unroll 1
+        for (int c = 0; c < G; ++c) {
+            if (4 * (uint64_t)c >= rem) break;
+            uint32_t ww[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ww[u] = 0;
+                if (4 * (uint64_t)c + u < rem) {
+                    uint64_t zn = gm_step<GEN>(zc, zp);
+                    zp = zc; zc = zn;
+                    ww[u] = gm_word<GEN>(pt ? gm_strip<GEN>(zn) : 0u, li, gmask);
+                }
+            }
+            if (c == li) { w0 = ww[0]; w1 = ww[1]; w2 = ww[2]; w3 = ww[3]; }
+        }
+        const uint64_t pos = 4 * (uint64_t)li;
+        if (vgroup && pos + 4 <= rem) {
+            store4<OutT>(o + base + pos, Cvt<OutT>::f(w0), Cvt<OutT>::f(w1), Cvt<OutT>::f(w2), Cvt<OutT>::f(w3));
+        } else {
+            if (pos < rem) o[base + pos] = Cvt<OutT>::f(w0);
+            if (pos + 1 < rem) o[base + pos + 1] = Cvt<OutT>::f(w1);
+            if (pos + 2 < rem) o[base + pos + 2] = Cvt<OutT>::f(w2);
+            if (pos + 3 < rem) o[base + pos + 3] = Cvt<OutT>::f(w3);
+        }
+    }
+    if (pt && start + len == nper) {
+        state_out[j * P::s + li] = zp << P::t;
+        state_out[(nstreams + j) * P::s + li] = zc << P::t;
+    }
+}
+
+// ----------------------------------------------------------------- host side
+template <int GEN>
+inline prand_status_t gm_build_table_t(uint64_t *tab, cudaStream_t st)
+{
+    gm_table_kernel<GEN><<<1, 32, 0, st>>>(tab);
+    return launch_check();
+}
+
+inline unsigned gm_grid_for(uint64_t n, unsigned block) { return (unsigned)((n + block - 1) / block); }
+
+template <int GEN>
+struct GmHost {
+    static prand_status_t seed(const uint64_t *tab, uint64_t *base, uint64_t seed, cudaStream_t st)
+    {
+        gm_seed_kernel<GEN><<<1, 32, 0, st>>>(tab, base, seed);
+        return launch_check();
+    }
+    static prand_status_t init(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n,
+                               cudaStream_t st)
+    {
+        const unsigned B = 128;
+        gm_init_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, base, state, first, n);
+        return launch_check();
+    }
+    static prand_status_t skip(const uint64_t *tab, uint64_t *state, uint64_t n, const U256 &off, cudaStream_t st)
+    {
+        const unsigned B = 128;
+        gm_skip_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, state, n, off);
+        return launch_check();
+    }
+    template <typename OutT>
+    static prand_status_t gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, uint64_t nstreams, OutT *out,
+                              uint64_t nper, cudaStream_t st, bool *swapped)
+    {
+        constexpr int G = GmT<GEN>::lanes;
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // groups to fill the GPU: 64 resident warps per SM worth of lanes
+        uint64_t target = (uint64_t)sms * 64 * (32 / G);
+        uint64_t s = nstreams < target ? (target + nstreams - 1) / nstreams : 1;
+        uint64_t maxs = nper / (16 * G) ? nper / (16 * G) : 1;
+        if (s > maxs) s = maxs;
+        if (s > 65535) s = 65535;
+        uint64_t seclen = (nper + s - 1) / s;
+        seclen = (seclen + 4 * G - 1) / (4 * G) * (4 * G);
+        if (seclen == 0) seclen = 4 * G;
+        uint32_t nsec = (uint32_t)((nper + seclen - 1) / seclen);
+        if (nsec == 0) nsec = 1;
+        int vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0;
+        const unsigned B = 256;
+        uint64_t *sout = nsec > 1 ? spare : state;
+        *swapped = nsec > 1;
+        gm_gen_kernel<GEN, OutT><<<gm_grid_for(nstreams * nsec * G, B), B, 0, st>>>(tab, state, sout, nstreams, nper, nsec,
+                                                                                 seclen, out, vec);
+        return launch_check();
+    }
+};
+
+
+// Per-generator entry points, instantiated one translation unit per generator.
+#define PRAND_GM_INSTANTIATE(GEN, NAME)                                                                          \
+    prand_status_t NAME##_table(uint64_t *tab, cudaStream_t st) { return gm_build_table_t<GEN>(tab, st); }      \
+    prand_status_t NAME##_seed(const uint64_t *tab, uint64_t *base, uint64_t seed, cudaStream_t st)            \
+    {                                                                                                         \
+        return GmHost<GEN>::seed(tab, base, seed, st);                                                        \
+    }                                                                                                         \
+    prand_status_t NAME##_init(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first,     \
+                               uint64_t n, cudaStream_t st)                                                   \
+    {                                                                                                         \
+        return GmHost<GEN>::init(tab, base, state, first, n, st);                                             \
+    }                                                                                                         \
+    prand_status_t NAME##_skip(const uint64_t *tab, uint64_t *state, uint64_t n, const U256 &off,             \
+                               cudaStream_t st)                                                               \
+    {                                                                                                         \
+        return GmHost<GEN>::skip(tab, state, n, off, st);                                                     \
+    }                                                                                                         \
+    prand_status_t NAME##_gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, uint64_t nstreams,       \
+                              void *out, int dtype, uint64_t nper, cudaStream_t st, bool *sw)                  \
+    {                                                                                                         \
+        if (dtype == PRAND_DTYPE_U32)                                                                         \
+            return GmHost<GEN>::template gen<uint32_t>(tab, state, spare, nstreams, (uint32_t *)out, nper, st, sw); \
+        if (dtype == PRAND_DTYPE_F32)                                                                         \
+            return GmHost<GEN>::template gen<float>(tab, state, spare, nstreams, (float *)out, nper, st, sw);  \
+        return GmHost<GEN>::template gen<double>(tab, state, spare, nstreams, (double *)out, nper, st, sw);    \
+    }
+
+}  // namespace prand

@@ -1,0 +1,107 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "../../include/prand.h"
+
+namespace prand {
+
+// ---------------------------------------------------------------------------
+// Generator constants, restated from the paper.
+// ---------------------------------------------------------------------------
+
+// MT19937 (Matsumoto & Nishimura 1998; Sec. 5.4).
+constexpr int kMtN = 624;
+constexpr int kMtM = 397;
+constexpr int kMtDeg = 19937;          // state dimension over GF(2)
+constexpr int kMtPolyWords = 624;      // 32-bit words per jump polynomial (19968 bits)
+constexpr int kMtPolyCount = 512;      // stored x^(2^b) mod phi, b = 0..511 (Sec. 5.4)
+constexpr int kMtStreamShift = 432;    // L = 2^432 >= 1e130 (Table 4)
+
+// MRG32K3A (Sec. 5.2).
+constexpr uint32_t kM1 = 4294967087u;  // 2^32 - 209
+constexpr uint32_t kM2 = 4294944443u;  // 2^32 - 22853
+constexpr int kMrgStreamShift = 127;   // L = 2^127 >= 1e38 (Table 4)
+
+// LFSR113 (Sec. 5.3): (p, q, s) per component.
+constexpr int kLfsrStreamShift = 34;   // L = 2^34 >= 1e10 (Table 4)
+
+// Jump tables hold M^(2^b) for b < kJumpBits (offsets up to 2^256).
+constexpr int kJumpBits = 256;
+
+// GM / GQ ensembles (Sec. 5.1, Table 2).  All arithmetic is done on z = x / 2^t
+// modulo the prime p (for GM55 and GQ58.x, g = 2^t p and k, q are even, so the
+// states used here are multiples of 2^t and x = 2^t z follows the same map mod p).
+enum PrimeKind { P19 = 0, P29 = 1, P31 = 2, P51 = 3, P61 = 4 };
+
+struct GmParams {
+    uint64_t k, q, p;  // recurrence z' = k z - q z_prev (mod p)
+    int t;             // g = 2^t p
+    int v;             // output bits per point
+    int s;             // points per output word
+    int lanes;         // lanes per stream group (power of two >= s)
+    PrimeKind kind;
+    uint64_t L;        // block length (Table 4 maximal length)
+    uint64_t nmax;     // number of sequences (Table 4)
+};
+
+inline bool is_gm(int gen) { return gen >= PRAND_GM19 && gen <= PRAND_GQ58_4; }
+const GmParams &gm_params(int gen);
+
+// Block length L as a 64-bit value for GM/GQ and the Table 4 capacity per generator.
+uint64_t table4_nmax(int gen);
+
+// ---------------------------------------------------------------------------
+// Per-device jump tables.
+// ---------------------------------------------------------------------------
+struct DevTables {
+    int device = -1;
+    uint32_t *mrg = nullptr;      // [kJumpBits][18]: A^(2^b) mod m1 (9 words), B^(2^b) mod m2 (9 words)
+    uint32_t *lfsr = nullptr;     // [4][kJumpBits][32]: column images of T_c^(2^b)
+    uint64_t *gm[8] = {};         // per GM/GQ generator: [kJumpBits][4] = M^(2^b) mod p
+    uint32_t *mt = nullptr;       // [kMtPolyCount][kMtPolyWords]: x^(2^b) mod phi
+    bool ready_basic = false;
+    bool ready_mt = false;
+};
+
+// Returns the tables of the current device, building what `gen` needs.
+prand_status_t get_tables(int gen, DevTables **out);
+
+// Host side of the MT19937 jump: characteristic polynomial (Berlekamp-Massey)
+// and the squaring chain x^(2^b) mod phi, b < count; each polynomial as 624
+// little-endian 32-bit words.  Computed once per process.
+const uint32_t *mt_host_pow2_polys();
+
+// ---------------------------------------------------------------------------
+// Handles.
+// ---------------------------------------------------------------------------
+struct prand_handle_impl;
+
+// Counting launches (all kernels go through launch_check()).
+extern std::atomic<uint64_t> g_launches;
+prand_status_t launch_check();  // cudaGetLastError after a launch; counts it
+
+// Offsets as 256-bit little-endian numbers.
+struct U256 { uint64_t w[4]; };
+
+// Family-specific device work, all asynchronous on `st` unless noted.
+// Base state of one "stream" in the family's device layout.
+prand_status_t seed_base(int gen, uint64_t seed, void *d_base, cudaStream_t st);
+// State bytes per stream in the family's device layout.
+size_t state_bytes_per_stream(int gen);
+// streams j = 0..n-1 := base advanced by (first + j) * L
+prand_status_t init_streams_dev(int gen, const DevTables *T, const void *d_base, void *d_state,
+                                uint64_t first, uint64_t n, cudaStream_t st);
+// all streams += off
+prand_status_t skipahead_dev(int gen, const DevTables *T, void *d_state, uint64_t n, uint32_t *mt_idx,
+                             const U256 &off, cudaStream_t st);
+// generate
+prand_status_t generate_dev(int gen, const DevTables *T, void *d_state, uint64_t nstreams, uint32_t *mt_idx,
+                            void *out, int dtype, uint64_t nper, cudaStream_t st);
+
+}  // namespace prand

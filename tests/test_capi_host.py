@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every entry point include/prand.h declares, and rejects
+bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1307_5869_gb300 as P
+from paper_1307_5869_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "prand.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(prand_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(P.EXPORTS)
+
+
+def test_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = P.prand_status_string(code)
+        assert s and s != "unknown status"
+    assert P.prand_status_string(99) == "unknown status"
+
+
+def test_argument_errors_without_device(lib):
+    L = lib
+    h = ctypes.c_void_p()
+    assert L.prand_create(None, 0, 0) == 1                       # NULL out
+    assert L.prand_create(ctypes.byref(h), 11, 0) == 1           # gen out of range
+    assert L.prand_create(ctypes.byref(h), -1, 0) == 1
+    assert L.prand_init_streams(None, 0, 1) == 1
+    assert L.prand_generate_u32(None, None, 1, None) == 1
+    assert L.prand_generate_f64(None, None, 1, None) == 1
+    assert L.prand_skipahead(None, None) == 1
+    n = ctypes.c_size_t(0)
+    assert L.prand_get_state(None, None, ctypes.byref(n)) == 1
+    assert L.prand_set_state(None, None, 0) == 1
+    assert L.prand_query(None, None, None, None) == 1
+    assert L.prand_destroy(None) == 0
+    bad = (P.Request * 1)(P.Request(42, 0, 0, 1, 0))
+    assert L.prand_batch_run(bad, 1, 0, None) == 1
+    bad = (P.Request * 1)(P.Request(0, 7, 0, 1, 0))
+    assert L.prand_batch_run(bad, 1, 0, None) == 1
+    assert L.prand_batch_run(None, 0, 0, None) == 0              # empty batch
+
+
+def test_binding_raises_on_error(lib):
+    with pytest.raises(P.PrandError):
+        P._check(1, "prand_init_streams")
+    assert P._check(7, "prand_init_streams", allow_warn=True) == 7
+    with pytest.raises(ValueError):
+        P.prand_skipahead(0, -1)

@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Every comparison is bit-exact: u32 outputs as integers, f32/f64 outputs with
+0 ulp (compared as raw bit patterns).  Inputs are seeded and synthetic.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1307_5869_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+GENS = P.GENERATORS
+NPDT = {"u32": np.uint32, "f32": np.uint32, "f64": np.uint64}
+
+
+def _bits(a: np.ndarray, dt: str) -> np.ndarray:
+    return np.ascontiguousarray(a).view(NPDT[dt])
+
+
+def _gpu(t) -> np.ndarray:
+    return t.cpu().numpy()
+
+
+def _assert_same(got, ref, dt, what=""):
+    g = _bits(got, dt)
+    r = _bits(ref, dt)
+    assert g.shape == r.shape, (what, g.shape, r.shape)
+    if not np.array_equal(g, r):
+        bad = np.argwhere(g != r)
+        i = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {i}: got {g[i]:#x} want {r[i]:#x}")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    P.load(build_if_missing=True)
+    torch.cuda.init()
+    yield
+
+
+@pytest.mark.parametrize("dt", ["u32", "f32", "f64"])
+@pytest.mark.parametrize("gen", GENS)
+def test_ragged_chunks_many_streams(gen, dt):
+    # 37 streams starting at stream 3, consecutive calls of ragged lengths
+    g = P.Generator(gen, 12345, 3, 37)
+    ref = O.Streams(gen, 12345, 3, 37)
+    for n in (1, 5, 127, 4097):
+        _assert_same(_gpu(g.generate(n, dt)), ref.generate(dt, n), dt, f"{gen} {dt} chunk {n}")
+    g.close()
+
+
+@pytest.mark.parametrize("gen", GENS)
+def test_long_sections_and_continuation(gen):
+    # few streams, long outputs: one stream is split into sections reached by jumps
+    nper = 20000 if gen != "MT19937" else 5000
+    g = P.Generator(gen, 777, 0, 2)
+    ref = O.Streams(gen, 777, 0, 2)
+    for n in (nper, 777, 3 * nper + 1):
+        _assert_same(_gpu(g.generate(n, "u32")), ref.generate("u32", n), "u32", f"{gen} n={n}")
+    g.close()
+
+
+def test_mrg32k3a_default_state_one_stream_2_pow_20():
+    # one stream of MRG32K3A from the paper's default state, 2^20 outputs as u32 and f64
+    n = 1 << 20
+    for dt in ("u32", "f64"):
+        g = P.Generator("MRG32K3A", P.SEED_DEFAULT, 0, 1)
+        got = _gpu(g.generate(n, dt))
+        g.close()
+        ref = O.State("MRG32K3A")
+        want = ref.u32(n) if dt == "u32" else ref.f64(n)
+        _assert_same(got.reshape(-1), want, dt, f"MRG32K3A default {dt}")
+        if dt == "f64":
+            assert (got > 0).all() and (got < 1).all()
+
+
+@pytest.mark.parametrize("gen", GENS)
+def test_skipahead_offsets(gen):
+    g = P.Generator(gen, 4242, 10, 5)
+    states = [O.State.stream(gen, 4242, 10 + j) for j in range(5)]
+    got = _gpu(g.generate(100, "u32"))
+    want = np.stack([s.u32(100) for s in states])
+    _assert_same(got, want, "u32", f"{gen} pre-skip")
+    for off in (1, 523, 624, 10**6 + 3, 2**100 + 7):
+        g.skipahead(off)
+        for s in states:
+            s.jump(off)
+        got = _gpu(g.generate(300, "u32"))
+        want = np.stack([s.u32(300) for s in states])
+        _assert_same(got, want, "u32", f"{gen} after skip {off}")
+    g.close()
+
+
+@pytest.mark.parametrize("gen", GENS)
+def test_state_checkpoint_resume(gen):
+    a = P.Generator(gen, 99, 1, 4)
+    a.generate(333, "u32")
+    blob = a.get_state()
+    cont = _gpu(a.generate(500, "u32"))
+    b = P.Generator(gen, 1, 0, 1)
+    b.set_state(blob)
+    _assert_same(_gpu(b.generate(500, "u32")), cont, "u32", f"{gen} resume")
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("gen", GENS)
+def test_misaligned_output_scalar_path(gen):
+    import torch
+    g = P.Generator(gen, 5, 0, 3)
+    ref = O.Streams(gen, 5, 0, 3)
+    buf = torch.zeros(3 * 1001 + 1, dtype=torch.int32, device="cuda")
+    out = buf[1:]  # 4-byte aligned, not 16-byte aligned
+    P.prand_generate_u32(g.h, out.data_ptr(), 1001, torch.cuda.current_stream().cuda_stream)
+    got = _gpu(out).reshape(3, 1001)
+    _assert_same(got, ref.generate("u32", 1001), "u32", f"{gen} misaligned")
+    assert int(_gpu(buf)[0]) == 0  # nothing written before the output
+    g.close()
+
+
+def test_error_paths_on_device():
+    import torch
+    L = P.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert L.prand_create(ctypes.byref(h), 1, 1) == 0
+    buf = torch.zeros(64, dtype=torch.int32, device="cuda")
+    assert L.prand_generate_u32(h, buf.data_ptr(), 4, None) == 5          # no streams yet
+    assert L.prand_init_streams(h, 0, 0) == 1                              # zero streams
+    assert L.prand_init_streams(h, 2**64 - 1, 2) == 1                      # index overflow
+    assert L.prand_init_streams(h, 0, 4) == 0
+    assert L.prand_generate_u32(h, buf.data_ptr() + 1, 4, None) == 2      # misaligned
+    assert L.prand_generate_f64(h, buf.data_ptr() + 4, 2, None) == 2      # f64 needs 8 bytes
+    assert L.prand_generate_u32(h, buf.data_ptr(), 0, None) == 0           # no-op
+    assert L.prand_init_streams(h, 10**19 - 1, 2) == 7                     # beyond Table 4
+    assert L.prand_destroy(h) == 0
+
+
+@pytest.mark.parametrize("gen", GENS)
+def test_table4_streams_2_pow_16_by_2_pow_12_sampled(gen):
+    # all eleven generators, 2^16 block-split streams x 2^12 outputs (u32 and f32),
+    # seed 12345; sampled streams against the oracle's stream k = base + k * L
+    import torch
+    n, nper = 1 << 16, 1 << 12
+    rng = np.random.default_rng(2024)
+    sample = sorted({0, 1, 2, n - 1} | set(int(x) for x in rng.integers(0, n, 6)))
+    for dt in ("u32", "f32"):
+        g = P.Generator(gen, 12345, 0, n)
+        out = g.generate(nper, dt)
+        idx = torch.tensor(sample, device="cuda")
+        got = _gpu(out[idx])
+        g.close()
+        del out
+        want = np.stack([getattr(O.State.stream(gen, 12345, k), dt)(nper) for k in sample])
+        _assert_same(got, want, dt, f"{gen} {dt} sampled")
+
+
+@pytest.mark.parametrize("gen", ["MT19937", "LFSR113", "GM61"])
+def test_bulk_2_pow_20_streams_sampled(gen):
+    # 2^20 streams x 2^10 (2^30 outputs), u32 then f32 continuing; seed from a 64-bit counter
+    import torch
+    n, nper = 1 << 20, 1 << 10
+    seed = 0x9E3779B97F4A7C15
+    g = P.Generator(gen, seed, 0, n)
+    idx = torch.tensor([0, 1, 777, 65536, n // 2 + 3, n - 1], device="cuda")
+    u = g.generate(nper, "u32")
+    gu = _gpu(u[idx])
+    del u
+    f = g.generate(nper, "f32")
+    gf = _gpu(f[idx])
+    del f
+    g.close()
+    for row, k in enumerate(idx.tolist()):
+        st = O.State.stream(gen, seed, k)
+        _assert_same(gu[row], st.u32(nper), "u32", f"{gen} stream {k} u32")
+        _assert_same(gf[row], st.f32(nper), "f32", f"{gen} stream {k} f32")
+
+
+def test_batch_run_mixed_requests():
+    import torch
+    rng = np.random.default_rng(7)
+    reqs, bufs, meta = [], [], []
+    for i in range(24):
+        gen = GENS[i % len(GENS)]
+        dt = ["u32", "f32", "f64"][i % 3]
+        k = int(rng.integers(0, 10**19, dtype=np.uint64))
+        n = int(rng.integers(1, 3000))
+        t = torch.empty(n, dtype={"u32": torch.int32, "f32": torch.float32, "f64": torch.float64}[dt], device="cuda")
+        bufs.append(t)
+        reqs.append((gen, {"u32": 0, "f32": 1, "f64": 2}[dt], k, n, t.data_ptr()))
+        meta.append((gen, dt, k, n))
+    P.prand_batch_run(reqs, 12345, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for t, (gen, dt, k, n) in zip(bufs, meta):
+        st = O.State.stream(gen, 12345, k)
+        _assert_same(_gpu(t), getattr(st, dt)(n), dt, f"batch {gen} {dt} stream {k}")
