@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-stream generation hot path on GB300.
+
+Workload (bulk fill): MT19937, LFSR113 and GM61, 2^20 block-split streams each,
+2^10 u32 outputs per stream followed by 2^10 f32 outputs per stream (2^30 + 2^30
+outputs per generator), seed from a 64-bit counter.  One step = both fills for
+all three generators (6 kernel launches, 6 * 2^30 outputs).  Stream states are
+initialised (jump-ahead) once before timing and stay resident; their init time
+is reported separately.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead
+(on the host cores, a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1307_5869_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GSamples/s (uint32) per generator, 2^30 outputs; % of HBM-write/int-pipe roofline"
+UNIT = "GSamples/s"
+WORKLOAD = ("bulk fill: MT19937, LFSR113, GM61; 2^20 block-split streams x (2^10 u32 + 2^10 f32) "
+            "outputs per generator per step; seed = 0x9E3779B97F4A7C15 + rank")
+
+# Algorithmic work per output (measurement section).
+STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 16, "GM29": 32 * 16,
+               "GM31": 32 * 16, "GM55": 8 * 16, "GM61": 32 * 16, "GQ58_1": 32 * 16, "GQ58_3": 12 * 16,
+               "GQ58_4": 8 * 16}
+# int32 operations per torus point step for the 61-bit Mersenne modulus, times 32 points per word
+GM61_OPS_PER_WORD = 24 * 32
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle (CPU) legs
+
+def oracle_rates(budget_s: float = 6.0, streams: int = 4):
+    """Time the oracle (single thread, as it stands) generating u32 then f32
+    rounds of 2^10 outputs per stream on the first streams of the bulk fill.
+    Stream initialisation is not timed (as on the GPU)."""
+    import oracle as O
+    rates, detail = {}, {}
+    share = {"MT19937": 0.2, "LFSR113": 0.2, "GM61": 0.6}
+    for gen in W.BULK_GENERATORS:
+        st = O.Streams(gen, W.bulk_seed(0), 0, streams)
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            st.generate("u32", W.BULK_PER_STREAM)
+            st.generate("f32", W.BULK_PER_STREAM)
+            n += 2 * streams * W.BULK_PER_STREAM
+            if time.perf_counter() - t0 >= budget_s * share[gen]:
+                break
+        dt = time.perf_counter() - t0
+        rates[gen] = n / dt
+        detail[gen] = {"samples": n, "seconds": round(dt, 3)}
+    return rates, detail
+
+
+def mix_throughput(rates: dict) -> float:
+    """Whole-workload samples/s for equal sample counts per generator."""
+    per = 2 * W.BULK_STREAMS * W.BULK_PER_STREAM
+    total_t = sum(per / rates[g] for g in W.BULK_GENERATORS)
+    return len(W.BULK_GENERATORS) * per / total_t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    steps = []
+    for i in range(args.warmup + args.steps):
+        rates, detail = oracle_rates(budget_s=args.ref_budget)
+        if i >= args.warmup:
+            steps.append((rates, detail))
+    rates = {g: statistics.median(s[0][g] for s in steps) for g in W.BULK_GENERATORS}
+    value = mix_throughput(rates) / 1e9
+    per_step_ms = 1e3 * 3 * 2 * W.BULK_STREAMS * W.BULK_PER_STREAM / (value * 1e9)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: first 4 streams of each generator, u32+f32 rounds of 2^10, "
+                                   f"~{args.ref_budget:.0f} s of oracle time; extrapolated to the full mix",
+                         "per_generator_samples_per_s": {g: rates[g] for g in rates}},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU leg
+
+def run_gpu(args):
+    import torch
+    import paper_1307_5869_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.load(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    nS = args.streams or W.BULK_STREAMS
+    nP = args.per_stream or W.BULK_PER_STREAM
+    gens = args.gens.split(",") if args.gens else W.BULK_GENERATORS
+    handles, init_ms = {}, {}
+    for g in gens:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = P.prand_create(g, W.bulk_seed(rank))
+        P.prand_init_streams(h, rank * nS, nS)
+        init_ms[g] = 1e3 * (time.perf_counter() - t0)
+        handles[g] = h
+    U = torch.empty(nS * nP, dtype=torch.int32, device="cuda")
+    F = torch.empty(nS * nP, dtype=torch.float32, device="cuda")
+
+    def step(ev=None):
+        for g in gens:
+            if ev is not None:
+                ev[g][0].record(stream)
+            P.prand_generate_u32(handles[g], U.data_ptr(), nP, sp)
+            if ev is not None:
+                ev[g][1].record(stream)
+            P.prand_generate_f32(handles[g], F.data_ptr(), nP, sp)
+            if ev is not None:
+                ev[g][2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [{g: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for g in gens} for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = P.prand_kernel_launches()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = P.prand_kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_u = {g: statistics.mean(e[g][0].elapsed_time(e[g][1]) for e in evs) for g in gens}
+    ms_f = {g: statistics.mean(e[g][1].elapsed_time(e[g][2]) for e in evs) for g in gens}
+    samples_step = len(gens) * 2 * nS * nP
+    value = world * samples_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ----- rooflines (per launch, live CUDA-event durations)
+    hbm_peak, peak_src = _peaks()
+    rooflines = {}
+    for g in gens:
+        for dt, ms in (("u32", ms_u[g]), ("f32", ms_f[g])):
+            key = f"{g}.{dt}"
+            if g.startswith("GM") or g.startswith("GQ"):
+                ops = nS * nP * GM61_OPS_PER_WORD
+                rooflines[key] = {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12,
+                                  "peak": SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
+                                  "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9}
+            else:
+                byts = nS * nP * 4 + 2 * nS * STATE_BYTES[g]
+                rooflines[key] = {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9,
+                                  "traffic": None}
+            rooflines[key]["frac"] = rooflines[key]["achieved"] / rooflines[key]["peak"]
+    # dominant kernel = the launch with the largest share of the step
+    dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
+    R = rooflines[dom]
+    roofline = {"bound": R["bound"], "achieved": R["achieved"], "peak": R["peak"], "unit": R["unit"],
+                "frac": R["frac"], "traffic": R.get("traffic"), "kernel": dom,
+                "peak_source": ("unit counts: 152 SMs x 128 int32 lanes x 2070 MHz" if R["bound"] == "alu"
+                                else f"{peak_src} HBM copy GB/s")}
+    per_gen = {g: 2 * nS * nP / ((ms_u[g] + ms_f[g]) * 1e-3) / 1e9 for g in gens}
+
+    # ----- end to end: same step through host buffers (device -> pinned host copies inside)
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty(nS * nP, dtype=torch.int32, pin_memory=True)
+        hf = torch.empty(nS * nP, dtype=torch.float32, pin_memory=True)
+
+        def e2e_step():
+            for g in gens:
+                P.prand_generate_u32(handles[g], U.data_ptr(), nP, sp)
+                hu.copy_(U, non_blocking=True)
+                P.prand_generate_f32(handles[g], F.data_ptr(), nP, sp)
+                hf.copy_(F, non_blocking=True)
+            torch.cuda.synchronize()
+            return int(hu[0]) + int(hf[0] > 2)  # read back a result on the host
+
+        e2e_step()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * samples_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(gens) * nS * nP * 8,
+               "steps": args.e2e_steps}
+        del hu, hf
+
+    for h in handles.values():
+        P.prand_destroy(h)
+    del U, F
+    torch.cuda.empty_cache()
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "generators": gens, "n_streams_per_gpu": nS,
+                       "n_per_stream": [nP, nP], "outputs": ["u32", "f32"],
+                       "l2": "no flush: every step writes 8 GiB of outputs per generator (>> 129 MB L2)",
+                       "parallelism": f"{world} GPU(s), disjoint stream ranges, no collective"},
+            "roofline": roofline,
+            "rooflines": rooflines,
+            "per_generator_gsamples_per_s": per_gen,
+            "init_ms": init_ms,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+        }
+        if args.gens or args.streams or args.per_stream:
+            line["config"]["workload"] = f"custom: {','.join(gens)}; {nS} streams x ({nP} u32 + {nP} f32)"
+        if world == 1 and not args.no_cpu_baseline and not (args.gens or args.streams or args.per_stream):
+            rates, detail = oracle_rates(budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {
+                "value": mix_throughput(rates) / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"first 4 streams of each generator, u32+f32 rounds of 2^10 outputs, "
+                          f"~{args.cpu_budget:.0f} s of single-thread oracle time, extrapolated to the mix",
+                "per_generator_samples_per_s": rates, "detail": detail}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    # smaller cases of single kernels (profiling); the default is the bulk-fill workload
+    ap.add_argument("--gens", default="", help="comma list of generators (default MT19937,LFSR113,GM61)")
+    ap.add_argument("--streams", type=int, default=0)
+    ap.add_argument("--per-stream", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
