@@ -162,6 +162,28 @@ typedef struct {
  * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
 prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream);
 
+/* No counterpart in the paper.  MRG32K3A u32 generation that allocates no
+ * memory, for callers that cannot call cudaMalloc: code that owns all device
+ * memory through its own allocator or a fixed budget (a framework's caching
+ * allocator, a long-running service), or that runs where an allocation would
+ * synchronise the device or is not allowed.
+ * dev_state: the caller's states of n_streams MRG32K3A streams, structure of
+ * arrays, 6 * n_streams uint32 words: word c of stream j at dev_state[c *
+ * n_streams + j], c = x_n, x_{n-1}, x_{n-2}, y_n, y_{n-1}, y_{n-2} (the payload
+ * layout prand_get_state writes for an MRG32K3A handle).  The states are
+ * advanced in place by n_per_stream outputs.  dev_out as in prand_generate_u32.
+ * Scratch: a fixed device array inside the library (1.5 MB of next states for
+ * at most 65536 streams, plus an 18 KB jump table), kept by every GPU that
+ * loads the library until the process exits.  n_streams above 65536 returns
+ * PRAND_ERR_ARG.  The first call on a device sets that device up (looks up the
+ * array addresses and fills the table with one launch it waits for), so make
+ * the first call before any stream capture.  All calls share the scratch:
+ * calls that overlap on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  Asynchronous on `stream` after
+ * the first call.  Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_CUDA. */
+prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_state, uint64_t n_streams, uint32_t *dev_out,
+                                                   uint64_t n_per_stream, prand_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ STATUS = {0: "PRAND_OK", 1: "PRAND_ERR_ARG", 2: "PRAND_ERR_ALIGN", 3: "PRAND_ERR
 EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_generate_f32",
            "prand_generate_f64", "prand_skipahead", "prand_get_state", "prand_set_state",
            "prand_query", "prand_destroy", "prand_status_string", "prand_kernel_launches",
-           "prand_batch_run"]
+           "prand_batch_run", "prand_mrg32k3a_generate_u32_noalloc"]
 
 
 class PrandError(RuntimeError):
@@ -77,6 +77,7 @@ def load(build_if_missing: bool = False):
     L.prand_kernel_launches.argtypes = []
     L.prand_kernel_launches.restype = u64
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
+    L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
     for nm in EXPORTS:
         if nm not in ("prand_status_string", "prand_kernel_launches"):
             getattr(L, nm).restype = ctypes.c_int
@@ -171,6 +172,13 @@ def prand_batch_run(requests, seed: int, stream: int = 0) -> None:
     for i, (g, dt, s, n, p) in enumerate(reqs):
         arr[i] = Request(_gid(g), dt, s, n, p)
     _check(load().prand_batch_run(arr, len(reqs), ctypes.c_uint64(seed), stream), "prand_batch_run")
+
+
+def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out: int, n_per_stream: int,
+                                        stream: int = 0) -> None:
+    """MRG32K3A u32 fill on caller-held states without any device allocation."""
+    _check(load().prand_mrg32k3a_generate_u32_noalloc(dev_state, n_streams, dev_out, n_per_stream, stream),
+           "prand_mrg32k3a_generate_u32_noalloc")
 
 
 # ----------------------------------------------------------------- wrapper

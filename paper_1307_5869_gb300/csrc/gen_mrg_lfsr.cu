@@ -392,3 +392,92 @@ prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_
 }
 
 }  // namespace prand
+
+// =========================================================== no-allocation entry point
+// prand_mrg32k3a_generate_u32_noalloc: the MRG32K3A u32 fill on caller-held
+// states, for callers that must not allocate device memory.  Its scratch (the
+// next-state buffer used when streams are split into sections, and the jump
+// table the sections start from) lives in the file-scope device arrays below,
+// which every GPU that loads this library keeps until the process exits.
+#include <mutex>
+
+namespace prand {
+
+constexpr uint64_t kNoAllocMaxStreams = 1ull << 16;  // 65536 streams: 1.5 MB of next states
+static __device__ __align__(256) uint32_t g_noalloc_next[6 * kNoAllocMaxStreams];
+static __device__ __align__(256) uint32_t g_noalloc_tab[kJumpBits * 18];
+
+__global__ void mrg_copy_words_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint64_t words)
+{
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < words) dst[i] = src[i];
+}
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDev {
+    bool ready = false;
+    uint32_t *next = nullptr;  // device address of g_noalloc_next on this device
+    uint32_t *tab = nullptr;   // device address of g_noalloc_tab on this device
+};
+NoAllocDev g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: look up the device addresses of
+// the two arrays (their host-side names are only stand-ins) and fill the jump
+// table with one launch, waited for so later calls on any stream see it.
+prand_status_t noalloc_setup(cudaStream_t st, NoAllocDev **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PRAND_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDev &D = g_noalloc_dev[dev];
+    if (!D.ready) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_next) != cudaSuccess || !p) return PRAND_ERR_CUDA;
+        D.next = (uint32_t *)p;
+        p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_tab) != cudaSuccess || !p) return PRAND_ERR_CUDA;
+        D.tab = (uint32_t *)p;
+        mrg_table_kernel<<<1, 32, 0, st>>>(D.tab);
+        prand_status_t s = launch_check();
+        if (s != PRAND_OK) return s;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PRAND_ERR_CUDA;
+        D.ready = true;
+    }
+    *out = &D;
+    return PRAND_OK;
+}
+}  // namespace
+
+}  // namespace prand
+
+extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_state, uint64_t n_streams, uint32_t *dev_out,
+                                                               uint64_t n_per_stream, prand_stream_t stream)
+{
+    using namespace prand;
+    if (!dev_state || !dev_out || n_streams == 0) return PRAND_ERR_ARG;
+    if (n_streams > kNoAllocMaxStreams) return PRAND_ERR_ARG;  // beyond the fixed scratch
+    if ((uintptr_t)dev_state % 4 || (uintptr_t)dev_out % 4) return PRAND_ERR_ALIGN;
+    uint64_t total;
+    if (__builtin_mul_overflow(n_streams, n_per_stream, &total) || total > (UINT64_MAX >> 2)) return PRAND_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    NoAllocDev *D = nullptr;
+    prand_status_t s = noalloc_setup(st, &D);
+    if (s != PRAND_OK) return s;
+    if (n_per_stream == 0) return PRAND_OK;
+    uint32_t nsec;
+    uint64_t seclen;
+    pick_sections(n_streams, n_per_stream, &nsec, &seclen);
+    int vec = ((uintptr_t)dev_out % 16) == 0;
+    const unsigned B = 256;
+    uint32_t *sout = nsec > 1 ? D->next : dev_state;
+    mrg_gen_kernel<uint32_t><<<grid_for(n_streams * nsec, B), B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_per_stream,
+                                                                          nsec, seclen, dev_out, vec);
+    if ((s = launch_check()) != PRAND_OK) return s;
+    if (nsec > 1) {
+        mrg_copy_words_kernel<<<grid_for(6 * n_streams, B), B, 0, st>>>(D->next, dev_state, 6 * n_streams);
+        if ((s = launch_check()) != PRAND_OK) return s;
+    }
+    return PRAND_OK;
+}

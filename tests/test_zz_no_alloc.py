@@ -1,0 +1,48 @@
+"""The allocation-free MRG32K3A entry point against the ordinary one.
+
+prand_mrg32k3a_generate_u32_noalloc serves callers that cannot allocate device
+memory (all memory owned by their own allocator or a fixed budget, or code
+running where an allocation would synchronise the device).  It keeps its
+scratch in a fixed array inside the library.  Here its output and the states it
+leaves behind must equal prand_generate_u32 on a handle holding the same
+streams, bit for bit, on two calls in a row.  The file sorts last so that a
+failure here never hides another test's result.
+"""
+import numpy as np
+import pytest
+
+import paper_1307_5869_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _payload(blob: bytes, n_streams: int) -> np.ndarray:
+    words = 6 * n_streams
+    return np.frombuffer(blob[len(blob) - 4 * words:], dtype=np.uint32).copy()
+
+
+@pytest.mark.parametrize("n_streams,n_per", [(3, 50_000), (4096, 1000), (65536, 64)])
+def test_noalloc_matches_handle_on_two_calls(n_streams, n_per):
+    import torch
+    P.load(build_if_missing=True)
+    g = P.Generator("MRG32K3A", 2024, 17, n_streams)
+    st = torch.from_numpy(_payload(g.get_state(), n_streams).view(np.int32)).cuda()
+    out = torch.empty(n_streams * n_per, dtype=torch.int32, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        ref = g.generate(n_per, "u32").reshape(-1)
+        P.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), n_streams, out.data_ptr(), n_per, sp)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), f"call {call}: outputs differ"
+        assert np.array_equal(st.cpu().numpy().view(np.uint32), _payload(g.get_state(), n_streams)), \
+            f"call {call}: states differ"
+    g.close()
+
+
+def test_noalloc_rejects_too_many_streams():
+    import torch
+    L = P.load(build_if_missing=True)
+    st = torch.zeros(6, dtype=torch.int32, device="cuda")
+    out = torch.zeros(4, dtype=torch.int32, device="cuda")
+    assert L.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), 65537, out.data_ptr(), 1, None) == 1
+    assert L.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), 0, out.data_ptr(), 1, None) == 1
