@@ -172,6 +172,65 @@ __device__ __forceinline__ void store4<double>(double *p, double a, double b, do
     reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
 }
 
+// ---------------------------------------------------------------- row staging
+// Thread-per-stream generators produce one row of outputs per lane; written
+// directly, a warp store would scatter 32 small pieces over 32 rows.  Instead
+// each lane stages 128 bytes of its row in a padded shared-memory tile (pitch
+// 144 B, so 16-byte accesses are bank-conflict free on both sides) and the warp
+// writes the tile out as whole 128-byte row segments, four rows per store.
+constexpr int kTilePitch = 144;
+constexpr int kTileBytes = 32 * kTilePitch;  // per warp
+
+template <typename OutT>
+struct RowFill {
+    static constexpr int K = 128 / (int)sizeof(OutT);  // outputs per row chunk
+    static constexpr int E = 16 / (int)sizeof(OutT);   // outputs per 16-byte vector
+};
+
+// Emits `len` outputs of this lane's stream to dst (16-byte aligned rows), all
+// 32 lanes of the warp taking part (lanes with len 0 only help store).
+// next() returns the next 32-bit output; cvt converts it.
+template <typename OutT, typename Next, typename Conv>
+__device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, uint64_t len, unsigned char *tile, int lane)
+{
+    constexpr int K = RowFill<OutT>::K, E = RowFill<OutT>::E;
+    uint64_t maxlen = len;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) maxlen = max(maxlen, (uint64_t)__shfl_xor_sync(kFull, (unsigned long long)maxlen, d));
+    const uint64_t nch = (maxlen + K - 1) / K;
+    unsigned char *myrow = tile + lane * kTilePitch;
+    for (uint64_t ch = 0; ch < nch; ++ch) {
+        const uint32_t cnt = len > ch * K ? (uint32_t)min((uint64_t)K, len - ch * K) : 0u;
+#pragma unroll
+        for (int v = 0; v < K / E; ++v) {
+            if ((uint32_t)(v * E) < cnt) {
+                OutT vals[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) vals[e] = (uint32_t)(v * E + e) < cnt ? cvt(next()) : OutT(0);
+                *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
+            }
+        }
+        __syncwarp();
+        const unsigned long long mydst = (unsigned long long)(dst + ch * K);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = 4 * i + (lane >> 3);
+            OutT *rd = (OutT *)__shfl_sync(kFull, mydst, r);
+            const uint32_t rc = __shfl_sync(kFull, cnt, r);
+            const int col = (lane & 7) * E;
+            const unsigned char *src = tile + r * kTilePitch + 16 * (lane & 7);
+            if ((uint32_t)(col + E) <= rc) {
+                *reinterpret_cast<uint4 *>(rd + col) = *reinterpret_cast<const uint4 *>(src);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((uint32_t)(col + e) < rc) rd[col + e] = reinterpret_cast<const OutT *>(src)[e];
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Big offsets.
 __device__ __forceinline__ int u256_bit(const U256 &e, int b) { return (int)((e.w[b >> 6] >> (b & 63)) & 1u); }
 

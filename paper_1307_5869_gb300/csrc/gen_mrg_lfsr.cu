@@ -129,12 +129,39 @@ __device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_
 // last one may be shorter); the thread of the last section writes the stream's
 // next state to sout, a separate buffer when a stream has several sections (so
 // no thread reads a state that another thread has already replaced).
-template <typename OutT>
+template <typename OutT, bool ROWS = false>
 __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
                                                       uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                       OutT *__restrict__ out, int vec)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ROWS) {
+        // every lane of a warp takes part in the staged stores (256 threads per block)
+        __shared__ __align__(16) unsigned char tiles[8][kTileBytes];
+        const bool live = tid < nstreams * nsec;
+        const uint64_t j = live ? tid % nstreams : 0;
+        const uint64_t start = live ? (tid / nstreams) * seclen : 0;
+        const uint64_t len = (live && start < nper) ? min(seclen, nper - start) : 0;
+        uint32_t x0 = 0, x1 = 0, x2 = 0, y0 = 0, y1 = 0, y2 = 0;
+        if (len) {
+            x0 = state[j]; x1 = state[nstreams + j]; x2 = state[2 * nstreams + j];
+            y0 = state[3 * nstreams + j]; y1 = state[4 * nstreams + j]; y2 = state[5 * nstreams + j];
+            if (start) {
+                uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
+                for (int b = 0; b < 64; ++b)
+                    if ((start >> b) & 1u) mrg_apply_bit(tab, b, x, y);
+                x0 = x[0]; x1 = x[1]; x2 = x[2]; y0 = y[0]; y1 = y[1]; y2 = y[2];
+            }
+        }
+        fill_rows<OutT>([&]() { return mrg_next(x0, x1, x2, y0, y1, y2); },
+                        [](uint32_t u) { return Cvt<OutT, true>::f(u); }, out + j * nper + start, len,
+                        tiles[threadIdx.x >> 5], threadIdx.x & 31);
+        if (len && start + len == nper) {
+            sout[j] = x0; sout[nstreams + j] = x1; sout[2 * nstreams + j] = x2;
+            sout[3 * nstreams + j] = y0; sout[4 * nstreams + j] = y1; sout[5 * nstreams + j] = y2;
+        }
+        return;
+    }
     if (tid >= nstreams * nsec) return;
     uint64_t j = tid % nstreams;
     uint32_t sec = (uint32_t)(tid / nstreams);
@@ -265,12 +292,35 @@ __device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32
     return z0 ^ z1 ^ z2 ^ z3;
 }
 
-template <typename OutT>
+template <typename OutT, bool ROWS = false>
 __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
                                                        uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                        OutT *__restrict__ out, int vec)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ROWS) {
+        __shared__ __align__(16) unsigned char tiles[8][kTileBytes];
+        const bool live = tid < nstreams * nsec;
+        const uint64_t j = live ? tid % nstreams : 0;
+        const uint64_t start = live ? (tid / nstreams) * seclen : 0;
+        const uint64_t len = (live && start < nper) ? min(seclen, nper - start) : 0;
+        uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
+        if (len) {
+            z0 = state[j]; z1 = state[nstreams + j]; z2 = state[2 * nstreams + j]; z3 = state[3 * nstreams + j];
+            if (start) {
+                uint32_t z[4] = { z0, z1, z2, z3 };
+                for (int b = 0; b < 64; ++b)
+                    if ((start >> b) & 1u) lfsr_apply_bit(tab, b, z);
+                z0 = z[0]; z1 = z[1]; z2 = z[2]; z3 = z[3];
+            }
+        }
+        fill_rows<OutT>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
+                        out + j * nper + start, len, tiles[threadIdx.x >> 5], threadIdx.x & 31);
+        if (len && start + len == nper) {
+            sout[j] = z0; sout[nstreams + j] = z1; sout[2 * nstreams + j] = z2; sout[3 * nstreams + j] = z3;
+        }
+        return;
+    }
     if (tid >= nstreams * nsec) return;
     uint64_t j = tid % nstreams;
     uint32_t sec = (uint32_t)(tid / nstreams);
@@ -374,10 +424,16 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
     uint64_t threads = nstreams * nsec;
     uint32_t *sin = (uint32_t *)d_state, *sout = nsec > 1 ? (uint32_t *)d_spare : sin;
     *swapped = nsec > 1;
-    if (gen == PRAND_MRG32K3A)
-        mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
-    else
-        lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+    // staged row stores need every row start 16-byte aligned
+    constexpr uint64_t E = RowFill<OutT>::E;
+    const bool rows = ((uintptr_t)out % 16) == 0 && nper % E == 0 && seclen % E == 0;
+    if (gen == PRAND_MRG32K3A) {
+        if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+        else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+    } else {
+        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+    }
     return launch_check();
 }
 

@@ -43,62 +43,84 @@ PRAND_GM_TRAITS(PRAND_GQ58_4, 8, 48, (1ull << 29) - 3, 29, 4, 8, 8, P29, 8000000
 #undef PRAND_GM_TRAITS
 
 // ----------------------------------------------------------------- one step
-// z' = k z - q z_prev (mod p), computed as k z + q (p - z_prev) and folded.
+// z' = k z - q z_prev (mod p) with lazy residues: between steps z stays in
+// [0, p + slack) (slack below), so a step needs one fold and no final
+// comparison.  Every fold is written as S - h p (h = the bits above the prime's
+// width), which maps onto multiply-adds rather than mask/compare chains.
+// canon() returns the residue in [0, p); all lazy ranges are below 2p.
+template <int GEN>
+__device__ __forceinline__ uint64_t gm_canon(uint64_t z)
+{
+    constexpr uint64_t p = GmT<GEN>::p;
+    return z >= p ? z - p : z;
+}
+
 template <int GEN>
 __device__ __forceinline__ uint64_t gm_step(uint64_t zc, uint64_t zp);
 
+// p = 2^19 - 1; lazy z < 2^19 + 128
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM19>(uint64_t zc, uint64_t zp)
 {
     constexpr uint32_t p = (1u << 19) - 1;
-    uint32_t s = 15u * (uint32_t)zc + 28u * (p - (uint32_t)zp);  // < 43 * 2^19
-    s = (s & p) + (s >> 19);                                    // < 2^19 + 43
-    return s >= p ? s - p : s;
+    uint32_t t = 2u * p - (uint32_t)zp;                    // = -z_prev (mod p), > 0
+    uint32_t S = 15u * (uint32_t)zc + 28u * t;             // < 2^26
+    uint32_t h = S >> 19;
+    return S - h * p;                                      // (S mod 2^19) + h < 2^19 + 128
 }
+// p = 2^29 - 3; lazy z < 2^29 + 24
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM29>(uint64_t zc, uint64_t zp)
 {
-    constexpr uint32_t p = (1u << 29) - 3, m = (1u << 29) - 1;
-    uint32_t s = 4u * (uint32_t)zc + 2u * (p - (uint32_t)zp);   // < 6 * 2^29 < 2^32
-    s = (s & m) + 3u * (s >> 29);                               // < 2^29 + 18
-    return s >= p ? s - p : s;
+    constexpr uint32_t p = (1u << 29) - 3;
+    uint32_t S = 4u * (uint32_t)zc + (3u * p - 2u * (uint32_t)zp);  // 4z - 2y + 3p in (2^29 - 57, 2^32)
+    uint32_t h = S >> 29;                                  // <= 7
+    return S - h * p;                                      // (S mod 2^29) + 3h < 2^29 + 24
 }
+// p = 2^31 - 1; lazy z < 2^31 + 32
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM31>(uint64_t zc, uint64_t zp)
 {
-    constexpr uint64_t p = (1ull << 31) - 1;
-    uint64_t s = 11ull * zc + 14ull * (p - zp);                  // < 25 * 2^31
-    s = (s & p) + (s >> 31);                                     // < 2^31 + 25
-    return s >= p ? s - p : s;
+    constexpr uint32_t p = (1u << 31) - 1;
+    uint32_t t = 2u * p - (uint32_t)zp;                    // (0, 2^32)
+    uint64_t S = (uint64_t)(uint32_t)zc * 11u + (uint64_t)t * 14u;  // < 2^36
+    uint32_t h = (uint32_t)(S >> 31);
+    return (uint32_t)S - h * p;                            // (S mod 2^31) + h < 2^31 + 32
 }
+// p = 2^51 - 129; lazy z < 2^51 + 2^18
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t zc, uint64_t zp)
 {
-    constexpr uint64_t p = (1ull << 51) - 129, m = (1ull << 51) - 1;
-    uint64_t s = (zc << 8) + 176ull * (p - zp);                  // < 432 * 2^51 < 2^60
-    s = (s & m) + 129ull * (s >> 51);                            // < 2^51 + 2^16
-    return s >= p ? s - p : s;
+    constexpr uint64_t p = (1ull << 51) - 129;
+    uint64_t t = 2 * p - zp;                               // (0, 2^52)
+    uint64_t S = (zc << 8) + t * 176u;                     // < 2^61
+    uint64_t h = S >> 51;                                  // < 2^10
+    return S - h * p;                                      // (S mod 2^51) + 129 h < 2^51 + 2^18
 }
+// p = 2^61 - 1; lazy z < 2^61 + 256.  Limbs of 32 bits: four 32x32->64
+// multiply-adds give S = 24 z + 74 (2p - y) < 2^69 as (B, A.lo).
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM61>(uint64_t zc, uint64_t zp)
 {
-    constexpr uint64_t p = (1ull << 61) - 1;
-    // 24 zc + 74 (p - zp) < 98 * 2^61: a 68-bit sum kept as (hi, lo)
-    uint64_t a_lo = zc * 24ull, a_hi = __umul64hi(zc, 24ull);
-    uint64_t y = p - zp;
-    uint64_t b_lo = y * 74ull, b_hi = __umul64hi(y, 74ull);
-    uint64_t lo = a_lo + b_lo;
-    uint64_t hi = a_hi + b_hi + (lo < a_lo ? 1ull : 0ull);
-    uint64_t r = (lo & p) + ((hi << 3) | (lo >> 61));            // < 2^61 + 2^11
-    return r >= p ? r - p : r;
+    const uint64_t t = 0x3FFFFFFFFFFFFFFEull - zp;        // 2p - y, (0, 2^62)
+    const uint32_t z0 = (uint32_t)zc, z1 = (uint32_t)(zc >> 32);
+    const uint32_t t0 = (uint32_t)t, t1 = (uint32_t)(t >> 32);
+    const uint64_t A = (uint64_t)z0 * 24u + (uint64_t)t0 * 74u;
+    const uint64_t B = (uint64_t)z1 * 24u + (uint64_t)t1 * 74u + (A >> 32);
+    const uint32_t b0 = (uint32_t)B, b1 = (uint32_t)(B >> 32);
+    const uint32_t h = __funnelshift_r(b0, b1, 29);        // S >> 61 (< 2^8)
+    uint64_t R = (((uint64_t)b0 << 32) | (uint32_t)A) + h; // low 64 bits of S, plus h
+    return R - ((uint64_t)h << 61);                        // (S mod 2^61) + h < 2^61 + 256
 }
+// p = 2^29 - 3 (GQ58.x, z = x / 2^29); lazy z < 2^29 + 384
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_1>(uint64_t zc, uint64_t zp)
 {
-    constexpr uint64_t p = (1ull << 29) - 3, m = (1ull << 29) - 1;
-    uint64_t s = 8ull * zc + 48ull * (p - zp);                   // < 56 * 2^29
-    s = (s & m) + 3ull * (s >> 29);                              // < 2^29 + 168
-    return s >= p ? s - p : s;
+    constexpr uint32_t p = (1u << 29) - 3;
+    uint32_t t = 2u * p - (uint32_t)zp;                    // (0, 2^30)
+    uint64_t S = (uint64_t)(uint32_t)zc * 8u + (uint64_t)t * 48u;  // < 2^36
+    uint32_t h = (uint32_t)(S >> 29);                      // < 2^7
+    return (uint32_t)S - h * p;                            // (S mod 2^29) + 3h < 2^29 + 384
 }
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_3>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
@@ -106,19 +128,38 @@ template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_4>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
 
 // ----------------------------------------------------------------- strips
-// floor(2^v z / p) = floor(2^v x / g): the horizontal strip of the torus.
+// floor(2^v z / p) of the canonical residue = floor(2^v x / g): the strip of the
+// torus the point lies in, evaluated on the lazy value z.
 template <int GEN>
-__device__ __forceinline__ uint32_t gm_strip(uint64_t z)
+__device__ __forceinline__ bool gm_strip1(uint64_t z)  // v = 1: canonical z in [(p+1)/2, p)
 {
     using P = GmT<GEN>;
-    if (P::v == 1) return z > (P::p >> 1) ? 1u : 0u;  // p odd: 2z >= p  <=>  z > (p-1)/2
-    // p = 2^b - c: q0 = floor(2^v z / 2^b) <= answer <= q0 + 1
-    constexpr int b = P::kind == P51 ? 51 : 29;
-    constexpr uint64_t c = P::kind == P51 ? 129 : 3;
-    constexpr uint64_t m = (1ull << b) - 1;
-    uint64_t q0 = z >> (b - P::v);
-    uint64_t r = ((z << P::v) & m) + c * q0;  // 2^v z - q0 p
-    return (uint32_t)(q0 + (r >= P::p ? 1u : 0u));
+    if (P::kind == P61) {
+        // z < 2^61 + 256: bit 60 set and z != p  <=>  canonical z >= 2^60
+        return ((uint32_t)(z >> 32) & 0x10000000u) && z != P::p;
+    }
+    constexpr uint32_t half = (uint32_t)((P::p + 1) / 2);
+    return (uint32_t)z - half < (uint32_t)(P::p - half);
+}
+
+template <int GEN>
+__device__ __forceinline__ uint32_t gm_strip(uint64_t z)  // v = 3, 4
+{
+    using P = GmT<GEN>;
+    // p = 2^b - c: q0 = floor(2^v z / 2^b); floor(2^v z / p) = q0 + [r >= p] with
+    // r = 2^v z - q0 p.  A lazy z in [p, p + slack) gives 2^v, masked to 0.
+    if (P::kind == P51) {
+        constexpr uint64_t m = (1ull << 51) - 1;
+        uint64_t q0 = z >> (51 - P::v);
+        uint64_t r = ((z << P::v) & m) + 129u * q0;
+        return (uint32_t)(q0 + (r >= P::p ? 1u : 0u)) & ((1u << P::v) - 1u);
+    } else {
+        constexpr uint32_t m = (1u << 29) - 1;
+        uint32_t zz = (uint32_t)z;
+        uint32_t q0 = zz >> (29 - P::v);
+        uint32_t r = ((zz << P::v) & m) + 3u * q0;
+        return (q0 + (r >= (uint32_t)P::p ? 1u : 0u)) & ((1u << P::v) - 1u);
+    }
 }
 
 // ----------------------------------------------------------------- jumps
@@ -223,28 +264,37 @@ __global__ void gm_skip_kernel(const uint64_t *tab, uint64_t *state, uint64_t n,
 }
 
 // ----------------------------------------------------------------- generation
-// OR-combine the word over the group (all lanes of the group end with it).
+// One step of the lane's point and the group's output word (all lanes of the
+// group end with it): a ballot for v = 1 (lane i <-> bit i), an OR-reduction
+// over the group's lanes for v = 3, 4.
 template <int GEN>
-__device__ __forceinline__ uint32_t gm_word(uint32_t strip, int li, unsigned gmask)
+__device__ __forceinline__ uint32_t gm_next_word(uint64_t &zc, uint64_t &zp, bool pt, int li, unsigned gmask)
 {
     using P = GmT<GEN>;
-    if (P::v == 1) return __ballot_sync(gmask, strip);  // lanes == 32: lane i <-> bit i
-    uint32_t w = (li < P::s && P::v * li < 32) ? (strip << (P::v * li)) : 0u;
-#pragma unroll
-    for (int d = 1; d < P::lanes; d <<= 1) w |= __shfl_xor_sync(gmask, w, d);
-    return w;
+    const uint64_t zn = gm_step<GEN>(zc, zp);
+    zp = zc;
+    zc = zn;
+    if (P::v == 1) return __ballot_sync(gmask, pt && gm_strip1<GEN>(zn));
+    const uint32_t w = (pt && P::v * li < 32) ? (gm_strip<GEN>(zn) << (P::v * li)) : 0u;
+    return __reduce_or_sync(gmask, w);
 }
 
-// One group = one section of one stream.  A round makes up to 4 * lanes words;
-// lane li keeps words 4 li .. 4 li + 3 of the round and stores them together.
+// One group = one section of one stream.  A round makes 4 * lanes words; lane
+// li keeps words 4 li .. 4 li + 3 of the round and stores them together, so a
+// group writes 16 * lanes contiguous bytes per round.  Full rounds run without
+// bounds checks; the last, partial round steps exactly the remaining count.
 // Every point takes exactly `len` steps, so the group of the last section holds
 // the stream's next state and writes it to state_out (a separate buffer when a
 // stream is split into several sections, so no group reads a state another
 // group has already replaced).
-template <int GEN, typename OutT>
+// VEC (chosen on the host) means every row start is 16-byte aligned, so full
+// rounds leave as one 16-byte store per lane; otherwise as 4-byte stores.  The
+// two forms are separate kernels: a run-time branch between two stores of the
+// same values to the same addresses may be folded into the wider one.
+template <int GEN, typename OutT, bool VEC>
 __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
                                                      uint64_t *state_out, uint64_t nstreams, uint64_t nper,
-                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out, int vec)
+                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out)
 {
     using P = GmT<GEN>;
     constexpr int G = P::lanes;
@@ -264,38 +314,44 @@ __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict_
         if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
     }
     OutT *o = out + j * nper + start;
-    const bool vgroup = vec && (((j * nper + start) & 3u) == 0);
-    for (uint64_t base = 0; base < len; base += 4 * G) {
-        const uint64_t rem = len - base;
+    const uint64_t full = len / (4 * G);
+    for (uint64_t r = 0; r < full; ++r) {
         uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-#pragma unroll 1
+#pragma unroll 2
         for (int c = 0; c < G; ++c) {
-            if (4 * (uint64_t)c >= rem) break;
-            uint32_t ww[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                ww[u] = 0;
-                if (4 * (uint64_t)c + u < rem) {
-                    uint64_t zn = gm_step<GEN>(zc, zp);
-                    zp = zc; zc = zn;
-                    ww[u] = gm_word<GEN>(pt ? gm_strip<GEN>(zn) : 0u, li, gmask);
-                }
-            }
-            if (c == li) { w0 = ww[0]; w1 = ww[1]; w2 = ww[2]; w3 = ww[3]; }
+            const uint32_t a = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            const uint32_t b = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            const uint32_t d = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            const uint32_t e = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            if (c == li) { w0 = a; w1 = b; w2 = d; w3 = e; }
         }
-        const uint64_t pos = 4 * (uint64_t)li;
-        if (vgroup && pos + 4 <= rem) {
-            store4<OutT>(o + base + pos, Cvt<OutT>::f(w0), Cvt<OutT>::f(w1), Cvt<OutT>::f(w2), Cvt<OutT>::f(w3));
+        OutT *q = o + r * 4 * G + 4 * li;
+        if (VEC) {
+            store4<OutT>(q, Cvt<OutT>::f(w0), Cvt<OutT>::f(w1), Cvt<OutT>::f(w2), Cvt<OutT>::f(w3));
         } else {
-            if (pos < rem) o[base + pos] = Cvt<OutT>::f(w0);
-            if (pos + 1 < rem) o[base + pos + 1] = Cvt<OutT>::f(w1);
-            if (pos + 2 < rem) o[base + pos + 2] = Cvt<OutT>::f(w2);
-            if (pos + 3 < rem) o[base + pos + 3] = Cvt<OutT>::f(w3);
+            q[0] = Cvt<OutT>::f(w0); q[1] = Cvt<OutT>::f(w1); q[2] = Cvt<OutT>::f(w2); q[3] = Cvt<OutT>::f(w3);
         }
     }
+    const uint32_t rem = (uint32_t)(len - full * 4 * G);  // < 4 G
+    if (rem) {
+        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+        for (uint32_t k = 0; k < rem; ++k) {
+            const uint32_t w = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            if ((k >> 2) == (uint32_t)li) {
+                const uint32_t u = k & 3u;
+                w0 = u == 0 ? w : w0; w1 = u == 1 ? w : w1; w2 = u == 2 ? w : w2; w3 = u == 3 ? w : w3;
+            }
+        }
+        OutT *q = o + full * 4 * G + 4 * li;
+        const uint32_t pos = 4 * li;
+        if (pos < rem) q[0] = Cvt<OutT>::f(w0);
+        if (pos + 1 < rem) q[1] = Cvt<OutT>::f(w1);
+        if (pos + 2 < rem) q[2] = Cvt<OutT>::f(w2);
+        if (pos + 3 < rem) q[3] = Cvt<OutT>::f(w3);
+    }
     if (pt && start + len == nper) {
-        state_out[j * P::s + li] = zp << P::t;
-        state_out[(nstreams + j) * P::s + li] = zc << P::t;
+        state_out[j * P::s + li] = gm_canon<GEN>(zp) << P::t;
+        state_out[(nstreams + j) * P::s + li] = gm_canon<GEN>(zc) << P::t;
     }
 }
 
@@ -348,12 +404,15 @@ struct GmHost {
         if (seclen == 0) seclen = 4 * G;
         uint32_t nsec = (uint32_t)((nper + seclen - 1) / seclen);
         if (nsec == 0) nsec = 1;
-        int vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0;
+        // section starts are multiples of 4 G, so rows start 16-byte aligned when
+        // the output is aligned and n_per_stream is a multiple of 4
+        const bool vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0 && nper % 4 == 0;
         const unsigned B = 256;
         uint64_t *sout = nsec > 1 ? spare : state;
         *swapped = nsec > 1;
-        gm_gen_kernel<GEN, OutT><<<gm_grid_for(nstreams * nsec * G, B), B, 0, st>>>(tab, state, sout, nstreams, nper, nsec,
-                                                                                 seclen, out, vec);
+        const unsigned grid = gm_grid_for(nstreams * nsec * G, B);
+        if (vec) gm_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, state, sout, nstreams, nper, nsec, seclen, out);
+        else gm_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, state, sout, nstreams, nper, nsec, seclen, out);
         return launch_check();
     }
 };

@@ -7,7 +7,7 @@
 #include <atomic>
 #include <mutex>
 
-#include "../../include/prand.h"
+#include "prand.h"
 
 namespace prand {
 

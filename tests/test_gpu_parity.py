@@ -52,6 +52,18 @@ def test_ragged_chunks_many_streams(gen, dt):
     g.close()
 
 
+@pytest.mark.parametrize("dt", ["u32", "f32", "f64"])
+@pytest.mark.parametrize("gen", GENS)
+def test_aligned_chunks_vector_stores(gen, dt):
+    # lengths that are multiples of 4 keep every row 16-byte aligned: the vector
+    # and staged-row store paths (the ragged test above covers the scalar ones)
+    g = P.Generator(gen, 31, 5, 300)
+    ref = O.Streams(gen, 31, 5, 300)
+    for n in (64, 1000, 4096):
+        _assert_same(_gpu(g.generate(n, dt)), ref.generate(dt, n), dt, f"{gen} {dt} chunk {n}")
+    g.close()
+
+
 @pytest.mark.parametrize("gen", GENS)
 def test_long_sections_and_continuation(gen):
     # few streams, long outputs: one stream is split into sections reached by jumps
