@@ -300,6 +300,13 @@ def run_gpu(args):
     del U, F
     torch.cuda.empty_cache()
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = run_batched(P, torch, sp, args)
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = run_serving(P, args)
+
     line = None
     if rank == 0:
         line = {
@@ -317,6 +324,8 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "batched": batched,
+            "serving": serving,
         }
         if args.gens or args.streams or args.per_stream:
             line["config"]["workload"] = f"custom: {','.join(gens)}; {nS} streams x ({nP} u32 + {nP} f32)"
@@ -335,6 +344,84 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(P, torch, sp, args):
+    """The batched workload: 10^4 requests (generator uniform over the eleven,
+    stream uniform in [0, 1e19), length floor(2^(20 U)) u32 outputs), run as one
+    persistent launch replayed from a CUDA graph, after the tile tuner; compared
+    with the same requests as per-request plain launches (bit-identical output)."""
+    reqspec = W.batched_requests(10_000, seed=7)
+    total = sum(n for _, _, n, _ in reqspec)
+    buf = torch.empty(total, dtype=torch.int32, device="cuda")
+    reqs, o = [], 0
+    for gen, k, n, _ in reqspec:
+        reqs.append((gen, P.DTYPE_U32, k, n, buf.data_ptr() + 4 * o))
+        o += n
+    t0 = time.perf_counter()
+    tuned = P.prand_batch_autotune(reqs, 7, sp)
+    tune_s = time.perf_counter() - t0
+    plan = P.prand_batch_plan_create(reqs, 7)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        P.prand_batch_plan_launch(plan, sp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        P.prand_batch_plan_launch(plan, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fused_ms = e0.elapsed_time(e1) / reps
+    P.prand_batch_plan_destroy(plan)
+    fused_copy = buf.clone()
+    buf.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if not args.no_per_request:
+        P.prand_batch_run_per_request(reqs, 7, sp)
+        torch.cuda.synchronize()
+        per_ms = 1e3 * (time.perf_counter() - t0)
+        identical = bool(torch.equal(buf, fused_copy))
+    else:
+        per_ms, identical = None, None
+    del buf, fused_copy
+    torch.cuda.empty_cache()
+    n_mt = sum(1 for g, _, _, _ in reqspec if g == "MT19937")
+    return {"workload": "10^4 requests, gen uniform over 11, stream uniform [0,1e19), length floor(2^(20U)) u32, seed 7",
+            "requests": len(reqspec), "outputs": total, "mt_requests": n_mt,
+            "fused_graph_ms": fused_ms, "fused_gsamples_per_s": total / (fused_ms * 1e-3) / 1e9,
+            "per_request_ms": per_ms,
+            "speedup_vs_per_request": (per_ms / fused_ms) if per_ms else None,
+            "outputs_identical": identical,
+            "tuned": {"seclen_mrg_lfsr": tuned[0], "seclen_gm": tuned[1], "best_ms": tuned[2], "tune_s": tune_s}}
+
+
+def run_serving(P, args):
+    """The serving workload: Poisson arrivals at 5e4 req/s for 10 s, each request
+    (generator uniform over the eleven, stream uniform in [0, 1e19), length
+    floor(2^(6 + 16 U)), dtype u32/f32/f64 equiprobable), replayed open-loop by
+    the library's native driver against the continuous-batching server."""
+    arr = W.serving_arrivals(rate=args.serve_rate, seconds=args.serve_seconds, seed=11)
+    reqs = [(g, d, k, n) for _, g, k, n, d in arr]
+    times = [t for t, _, _, _, _ in arr]
+    srv = P.prand_server_create(11, 8 << 30, 65536)
+    try:
+        lat, wall = P.prand_server_replay(srv, reqs, times)
+        st = P.prand_server_stats(srv)
+    finally:
+        P.prand_server_destroy(srv)
+    lat_ms = sorted(1e3 * x for x in lat)
+    samples = sum(n for _, _, _, n in reqs)
+    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(q * len(lat_ms)))]
+    return {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s; gen uniform over 11, "
+                        "stream uniform [0,1e19), length floor(2^(6+16U)), dtype u32/f32/f64 equiprobable",
+            "requests": len(reqs), "samples": samples, "wall_s": wall,
+            "gsamples_per_s": samples / wall / 1e9, "demanded_gsamples_per_s": samples / args.serve_seconds / 1e9,
+            "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat_ms[-1],
+            "resident_hit_rate": st["hits"] / max(1, st["hits"] + st["misses"] + st["restores"]),
+            "batches": st["batches"], "spills": st["spills"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,6 +431,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-per-request", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=5e4)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     # smaller cases of single kernels (profiling); the default is the bulk-fill workload

@@ -156,11 +156,88 @@ typedef struct {
     void *dev_out;    /* device pointer */
 } prand_request_t;
 
-/* Run n requests of mixed generators and uneven lengths (asynchronous on
- * `stream`).  Each request's output equals prand_init_streams(stream, 1) then
- * prand_generate_<dtype>(length) on a handle created with the same seed.
+/* Run n requests of mixed generators and uneven lengths in one persistent
+ * launch (asynchronous on `stream`): each request's jump to its stream and to
+ * the start of each of its sections (block splitting, Sec. 5 / Table 4) is
+ * fused in front of its generation; warps take tiles (sections of requests)
+ * from a shared counter, longest first.  Each request's output equals
+ * prand_init_streams(stream, 1) then prand_generate_<dtype>(length) on a handle
+ * created with the same seed.  The request array may be reused as soon as the
+ * call returns; the library keeps its own copy of the work list.
  * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
 prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream);
+
+/* The same requests, one ordinary stream-initialisation launch and one
+ * generation launch per request (no fusion, no persistent scheduling); the
+ * comparison point for prand_batch_run.  Returns after the work completes. */
+prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n, uint64_t seed,
+                                           prand_stream_t stream);
+
+/* A prepared batch: the work list is planned and uploaded once and the launch
+ * is captured in a CUDA graph, so prand_batch_plan_launch replays it with one
+ * graph launch.  Outputs go to the requests' dev_out pointers on every launch.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA;
+ * launch: PRAND_ERR_STATE if another device is current. */
+typedef struct prand_batch_plan_s *prand_batch_plan_t;
+prand_status_t prand_batch_plan_create(prand_batch_plan_t *plan, const prand_request_t *reqs, size_t n, uint64_t seed);
+prand_status_t prand_batch_plan_launch(prand_batch_plan_t plan, prand_stream_t stream);
+prand_status_t prand_batch_plan_destroy(prand_batch_plan_t plan);
+
+/* Tile tuner: times the batch for each candidate section length (outputs per
+ * lane for MRG32K3A/LFSR113, per lane group for GM/GQ), keeps the fastest for
+ * later batches on this device, and reports it (any output pointer may be
+ * NULL).  If the environment variable PRAND_TUNE_CACHE names a file, the
+ * result is written there and read back by later processes. */
+prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream,
+                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, float *best_ms);
+
+/* ---- Request server (continuous batching, resident streams) ----
+ * A request (generator, stream index, length, element type) returns the next
+ * `length` outputs of that stream: the server keeps each stream it has served
+ * resident on the device and continues it on the next request; a stream seen
+ * for the first time starts from the seed's base advanced by k * L (Table 4).
+ * A worker thread admits pending requests in arrival order while the output
+ * arena has room, launches them as batches of the persistent kernel on
+ * several CUDA streams (batches overlap on the device), and keeps requests on
+ * the same stream in order.  When a generator's slots are all taken, the least
+ * recently used idle stream's state moves to host memory and is restored on
+ * its next request, so results never depend on the order of other streams. */
+typedef struct prand_server_s *prand_server_t;
+typedef struct {
+    uint64_t completed, samples;  /* requests finished, outputs produced            */
+    uint64_t hits, misses;        /* requests that continued a resident stream / not */
+    uint64_t spills, restores;    /* states moved to host memory and back           */
+    uint64_t batches, pending;    /* batches launched, requests waiting now         */
+    uint64_t tiles;               /* work tiles launched                            */
+    double worker_busy_s;         /* worker time spent planning and launching       */
+} prand_server_stats_t;
+
+/* output_bytes: device arena for outputs (a request whose output does not fit
+ * is refused at submit); slots_per_generator: resident streams per generator.
+ * The server is bound to the current device; its worker thread makes that
+ * device current itself.  Errors: PRAND_ERR_ARG, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+prand_status_t prand_server_create(prand_server_t *srv, uint64_t seed, uint64_t output_bytes,
+                                   uint32_t slots_per_generator);
+/* Queue a request; *id identifies it.  Thread-safe.  Errors: PRAND_ERR_ARG. */
+prand_status_t prand_server_submit(prand_server_t srv, int32_t gen, uint64_t stream, uint64_t length, int32_t dtype,
+                                   uint64_t *id);
+/* *done = 1 once the outputs are on the device at *dev_out (valid until
+ * prand_server_release); *latency_s = completion time - submit time. */
+prand_status_t prand_server_query(prand_server_t srv, uint64_t id, int32_t *done, void **dev_out, double *latency_s);
+/* Copy the first `bytes` of a completed request's output to host memory. */
+prand_status_t prand_server_read(prand_server_t srv, uint64_t id, void *host_dst, uint64_t bytes);
+/* Ids of requests completed since the last call (at most cap; *n = count). */
+prand_status_t prand_server_completed(prand_server_t srv, uint64_t *ids, size_t cap, size_t *n);
+/* Return a completed request's output memory to the arena. */
+prand_status_t prand_server_release(prand_server_t srv, uint64_t id);
+prand_status_t prand_server_stats(prand_server_t srv, prand_server_stats_t *stats);
+/* Stops the worker after the batches in flight; outstanding outputs are freed. */
+prand_status_t prand_server_destroy(prand_server_t srv);
+/* Open-loop load driver: submits reqs[i] (dev_out ignored) arrival_s[i] seconds
+ * after the call, releases outputs as they complete, and writes each request's
+ * latency; *wall_s = time until the last completion. */
+prand_status_t prand_server_replay(prand_server_t srv, const prand_request_t *reqs, const double *arrival_s, size_t n,
+                                   double *latency_s, double *wall_s);
 
 /* No counterpart in the paper.  MRG32K3A u32 generation that allocates no
  * memory, for callers that cannot call cudaMalloc: code that owns all device

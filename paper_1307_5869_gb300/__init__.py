@@ -33,13 +33,22 @@ STATUS = {0: "PRAND_OK", 1: "PRAND_ERR_ARG", 2: "PRAND_ERR_ALIGN", 3: "PRAND_ERR
 EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_generate_f32",
            "prand_generate_f64", "prand_skipahead", "prand_get_state", "prand_set_state",
            "prand_query", "prand_destroy", "prand_status_string", "prand_kernel_launches",
-           "prand_batch_run", "prand_mrg32k3a_generate_u32_noalloc"]
+           "prand_batch_run", "prand_batch_run_per_request", "prand_batch_plan_create",
+           "prand_batch_plan_launch", "prand_batch_plan_destroy", "prand_batch_autotune",
+           "prand_mrg32k3a_generate_u32_noalloc", "prand_server_create", "prand_server_submit",
+           "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
+           "prand_server_destroy", "prand_server_replay"]
 
 
 class PrandError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
         super().__init__(f"{where}: {STATUS.get(status, status)} ({_status_text(status)})")
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_uint64) for nm in ("completed", "samples", "hits", "misses", "spills", "restores",
+                                                 "batches", "pending", "tiles")] + [("worker_busy_s", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -78,6 +87,25 @@ def load(build_if_missing: bool = False):
     L.prand_kernel_launches.restype = u64
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
     L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
+    vp = ctypes.c_void_p
+    L.prand_server_create.argtypes = [ctypes.POINTER(vp), u64, u64, ctypes.c_uint32]
+    L.prand_server_submit.argtypes = [vp, ctypes.c_int32, u64, u64, ctypes.c_int32, ctypes.POINTER(u64)]
+    L.prand_server_query.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vp),
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.prand_server_completed.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.prand_server_release.argtypes = [vp, u64]
+    L.prand_server_read.argtypes = [vp, u64, vp, u64]
+    L.prand_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.prand_server_destroy.argtypes = [vp]
+    L.prand_server_replay.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double), ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.prand_batch_run_per_request.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
+    L.prand_batch_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Request), ctypes.c_size_t, u64]
+    L.prand_batch_plan_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.prand_batch_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.prand_batch_autotune.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_float)]
     for nm in EXPORTS:
         if nm not in ("prand_status_string", "prand_kernel_launches"):
             getattr(L, nm).restype = ctypes.c_int
@@ -165,13 +193,49 @@ def prand_kernel_launches() -> int:
     return int(load().prand_kernel_launches())
 
 
-def prand_batch_run(requests, seed: int, stream: int = 0) -> None:
-    """requests: iterable of (gen, dtype, stream_index, length, dev_ptr)."""
+def requests_array(requests):
+    """(gen, dtype, stream_index, length, dev_ptr) tuples -> a prand_request_t array."""
     reqs = list(requests)
     arr = (Request * max(1, len(reqs)))()
     for i, (g, dt, s, n, p) in enumerate(reqs):
         arr[i] = Request(_gid(g), dt, s, n, p)
-    _check(load().prand_batch_run(arr, len(reqs), ctypes.c_uint64(seed), stream), "prand_batch_run")
+    return arr, len(reqs)
+
+
+def prand_batch_run(requests, seed: int, stream: int = 0) -> None:
+    """requests: iterable of (gen, dtype, stream_index, length, dev_ptr)."""
+    arr, n = requests_array(requests)
+    _check(load().prand_batch_run(arr, n, ctypes.c_uint64(seed), stream), "prand_batch_run")
+
+
+def prand_batch_run_per_request(requests, seed: int, stream: int = 0) -> None:
+    arr, n = requests_array(requests)
+    _check(load().prand_batch_run_per_request(arr, n, ctypes.c_uint64(seed), stream), "prand_batch_run_per_request")
+
+
+def prand_batch_plan_create(requests, seed: int) -> int:
+    arr, n = requests_array(requests)
+    p = ctypes.c_void_p()
+    _check(load().prand_batch_plan_create(ctypes.byref(p), arr, n, ctypes.c_uint64(seed)), "prand_batch_plan_create")
+    return p.value
+
+
+def prand_batch_plan_launch(plan: int, stream: int = 0) -> None:
+    _check(load().prand_batch_plan_launch(plan, stream), "prand_batch_plan_launch")
+
+
+def prand_batch_plan_destroy(plan: int) -> None:
+    if plan:
+        _check(load().prand_batch_plan_destroy(plan), "prand_batch_plan_destroy")
+
+
+def prand_batch_autotune(requests, seed: int, stream: int = 0):
+    """Returns (seclen_mrg_lfsr, seclen_gm, best_ms) and keeps them for later batches."""
+    arr, n = requests_array(requests)
+    a, b, t = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    _check(load().prand_batch_autotune(arr, n, ctypes.c_uint64(seed), stream, ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(t)), "prand_batch_autotune")
+    return a.value, b.value, t.value
 
 
 def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out: int, n_per_stream: int,
@@ -179,6 +243,68 @@ def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out:
     """MRG32K3A u32 fill on caller-held states without any device allocation."""
     _check(load().prand_mrg32k3a_generate_u32_noalloc(dev_state, n_streams, dev_out, n_per_stream, stream),
            "prand_mrg32k3a_generate_u32_noalloc")
+
+
+def prand_server_create(seed: int, output_bytes: int, slots_per_generator: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().prand_server_create(ctypes.byref(h), ctypes.c_uint64(seed), output_bytes, slots_per_generator),
+           "prand_server_create")
+    return h.value
+
+
+def prand_server_submit(srv: int, gen, stream: int, length: int, dtype: int) -> int:
+    i = ctypes.c_uint64()
+    _check(load().prand_server_submit(srv, _gid(gen), stream, length, dtype, ctypes.byref(i)), "prand_server_submit")
+    return i.value
+
+
+def prand_server_query(srv: int, rid: int):
+    """(done, device pointer or None, latency seconds)."""
+    d, p, lat = ctypes.c_int32(), ctypes.c_void_p(), ctypes.c_double()
+    _check(load().prand_server_query(srv, rid, ctypes.byref(d), ctypes.byref(p), ctypes.byref(lat)),
+           "prand_server_query")
+    return bool(d.value), p.value, lat.value
+
+
+def prand_server_completed(srv: int, cap: int = 4096):
+    arr = (ctypes.c_uint64 * cap)()
+    n = ctypes.c_size_t()
+    _check(load().prand_server_completed(srv, arr, cap, ctypes.byref(n)), "prand_server_completed")
+    return [arr[i] for i in range(n.value)]
+
+
+def prand_server_read(srv: int, rid: int, out) -> None:
+    """Copy a completed request's output into the numpy array `out`."""
+    _check(load().prand_server_read(srv, rid, out.ctypes.data, out.nbytes), "prand_server_read")
+
+
+def prand_server_release(srv: int, rid: int) -> None:
+    _check(load().prand_server_release(srv, rid), "prand_server_release")
+
+
+def prand_server_stats(srv: int) -> dict:
+    st = ServerStats()
+    _check(load().prand_server_stats(srv, ctypes.byref(st)), "prand_server_stats")
+    return {nm: getattr(st, nm) for nm, _ in ServerStats._fields_}
+
+
+def prand_server_destroy(srv: int) -> None:
+    if srv:
+        _check(load().prand_server_destroy(srv), "prand_server_destroy")
+
+
+def prand_server_replay(srv: int, requests, arrivals):
+    """requests: (gen, dtype, stream, length) tuples; arrivals: seconds.  Returns (latencies, wall_s)."""
+    reqs = list(requests)
+    n = len(reqs)
+    arr = (Request * max(1, n))()
+    for i, (g, dt, k, L) in enumerate(reqs):
+        arr[i] = Request(_gid(g), dt, k, L, None)
+    at = (ctypes.c_double * max(1, n))(*arrivals)
+    lat = (ctypes.c_double * max(1, n))()
+    wall = ctypes.c_double()
+    _check(load().prand_server_replay(srv, arr, at, n, lat, ctypes.byref(wall)), "prand_server_replay")
+    return [lat[i] for i in range(n)], wall.value
 
 
 # ----------------------------------------------------------------- wrapper

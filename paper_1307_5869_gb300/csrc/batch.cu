@@ -1,0 +1,726 @@
+// Batched generation: thousands of requests (generator, stream index, length,
+// element type, output pointer) of mixed generators and uneven lengths in one
+// persistent launch, with each request's jump-ahead (block splitting, Table 4,
+// plus the offset of its section) fused in front of its generation.
+//
+// Work unit: a tile, run by one warp.  MRG32K3A / LFSR113 tiles are up to 32
+// sections of one request (one lane each, rows written through the staged
+// 128-byte row stores); GM/GQ tiles are up to 32 / lanes sections (one lane
+// group each); MT19937 tiles are one whole request (the jump is a chain of
+// polynomial applications by the warp, Sec. 5.4).  Warps claim tiles from an
+// atomic counter, so short and long tiles balance across the GPU; tiles are
+// ordered longest first.
+//
+// The same kernel serves the resident-stream server: a tile may start from a
+// state slot instead of the seeded base, and the tile that ends a request
+// writes the stream's next state back to its slot.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "batch.cuh"
+#include "gm_impl.cuh"
+#include "mrg_lfsr_dev.cuh"
+#include "mt_dev.cuh"
+
+namespace prand {
+
+prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                             cudaStream_t st);
+prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
+                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped);
+prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                       cudaStream_t st);
+prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out, int dtype,
+                      uint64_t nper, cudaStream_t st, bool *swapped);
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
+prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
+
+constexpr int kBatchThreads = 64;  // small blocks: a warp on a long tile (an MT19937 jump chain) holds little besides itself
+constexpr int kWarpSmem = 5120;  // max of: MT 2 x 624 words, staged row tile 32 x 144 B, GM word slots
+
+// ------------------------------------------------------------------ MRG / LFSR tiles
+template <typename OutT>
+__device__ __forceinline__ void batch_mrg(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
+{
+    const uint64_t off = (uint64_t)lane * T.seclen;
+    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
+    uint32_t x[3], y[3];
+    const bool from_slot = T.flags & kTileFromSlot;
+    const uint32_t *src = from_slot ? (const uint32_t *)C.slots[PRAND_MRG32K3A] + 6 * (uint64_t)T.slot
+                                    : (const uint32_t *)C.base[PRAND_MRG32K3A];
+    for (int i = 0; i < 3; ++i) { x[i] = src[i]; y[i] = src[3 + i]; }
+    if (len) {
+        if (!from_slot)
+            for (int b = 0; b < 64; ++b)
+                if ((T.stream >> b) & 1u) mrg_apply_bit(C.mrg_tab, kMrgStreamShift + b, x, y);
+        const uint64_t s = T.start + off;
+        for (int b = 0; b < 64; ++b)
+            if ((s >> b) & 1u) mrg_apply_bit(C.mrg_tab, b, x, y);
+    }
+    uint32_t x0 = x[0], x1 = x[1], x2 = x[2], y0 = y[0], y1 = y[1], y2 = y[2];
+    OutT *o = (OutT *)T.out + off;
+    if (T.flags & kTileVec) {
+        fill_rows<OutT>([&]() { return mrg_next(x0, x1, x2, y0, y1, y2); },
+                        [](uint32_t u) { return Cvt<OutT, true>::f(u); }, o, len, wsm, lane);
+    } else {
+        for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT, true>::f(mrg_next(x0, x1, x2, y0, y1, y2));
+    }
+    if ((T.flags & kTileLast) && len && off + len == T.len) {
+        uint32_t *d = (uint32_t *)C.slots[PRAND_MRG32K3A] + 6 * (uint64_t)T.wslot;
+        d[0] = x0; d[1] = x1; d[2] = x2; d[3] = y0; d[4] = y1; d[5] = y2;
+    }
+}
+
+template <typename OutT>
+__device__ __forceinline__ void batch_lfsr(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
+{
+    const uint64_t off = (uint64_t)lane * T.seclen;
+    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
+    uint32_t z[4];
+    const bool from_slot = T.flags & kTileFromSlot;
+    const uint32_t *src = from_slot ? (const uint32_t *)C.slots[PRAND_LFSR113] + 4 * (uint64_t)T.slot
+                                    : (const uint32_t *)C.base[PRAND_LFSR113];
+    for (int c = 0; c < 4; ++c) z[c] = src[c];
+    if (len) {
+        // exponent (slot ? 0 : stream * 2^34) + start + off, as 128 bits
+        const uint64_t s = T.start + off;
+        uint64_t lo = s, hi = 0;
+        if (!from_slot) {
+            const uint64_t klo = T.stream << kLfsrStreamShift, khi = T.stream >> (64 - kLfsrStreamShift);
+            lo = klo + s;
+            hi = khi + (lo < klo ? 1u : 0u);
+        }
+        for (int b = 0; b < 64; ++b)
+            if ((lo >> b) & 1u) lfsr_apply_bit(C.lfsr_tab, b, z);
+        for (int b = 0; b < 64; ++b)
+            if ((hi >> b) & 1u) lfsr_apply_bit(C.lfsr_tab, 64 + b, z);
+    }
+    uint32_t z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3];
+    OutT *o = (OutT *)T.out + off;
+    if (T.flags & kTileVec) {
+        fill_rows<OutT>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); }, o, len,
+                        wsm, lane);
+    } else {
+        for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(lfsr_next(z0, z1, z2, z3));
+    }
+    if ((T.flags & kTileLast) && len && off + len == T.len) {
+        uint32_t *d = (uint32_t *)C.slots[PRAND_LFSR113] + 4 * (uint64_t)T.wslot;
+        d[0] = z0; d[1] = z1; d[2] = z2; d[3] = z3;
+    }
+}
+
+// ------------------------------------------------------------------ GM / GQ tiles
+template <int GEN, typename OutT>
+__device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
+{
+    using P = GmT<GEN>;
+    constexpr int G = P::lanes;
+    const int grp = lane / G, li = lane % G;
+    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const uint64_t off = (uint64_t)grp * T.seclen;
+    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
+    if (len == 0) return;  // whole group
+    const bool pt = li < P::s;
+    const uint64_t *tab = C.gm_tab[GEN - PRAND_GM19];
+    const bool from_slot = T.flags & kTileFromSlot;
+    const uint64_t *src = from_slot ? (const uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.slot
+                                    : (const uint64_t *)C.base[GEN];
+    uint64_t zp = 0, zc = 0;
+    if (pt) {
+        zp = src[li] >> P::t;
+        zc = src[P::s + li] >> P::t;
+        // exponent (slot ? 0 : stream * L) + start + off, as 128 bits
+        const uint64_t s = T.start + off;
+        uint64_t lo = s, hi = 0;
+        if (!from_slot) {
+            const uint64_t klo = T.stream * P::L_, khi = __umul64hi(T.stream, P::L_);
+            lo = klo + s;
+            hi = khi + (lo < klo ? 1u : 0u);
+        }
+        gm_jump128<GEN>(tab, lo, hi, zc, zp);
+    }
+    OutT *o = (OutT *)T.out + off;
+    uint32_t *myslot = reinterpret_cast<uint32_t *>(wsm) + 4 * lane;
+    if (T.flags & kTileVec) gm_generate_section<GEN, OutT, true>(zc, zp, pt, li, gmask, o, len, myslot);
+    else gm_generate_section<GEN, OutT, false>(zc, zp, pt, li, gmask, o, len, myslot);
+    if ((T.flags & kTileLast) && pt && off + len == T.len) {
+        uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
+        d[li] = gm_canon<GEN>(zp) << P::t;
+        d[P::s + li] = gm_canon<GEN>(zc) << P::t;
+    }
+}
+
+// ------------------------------------------------------------------ MT19937 tiles
+// Slot layout: 624 words of the current block, then the index inside it.
+template <typename OutT>
+__device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
+{
+    uint32_t *b0 = reinterpret_cast<uint32_t *>(wsm), *b1 = b0 + kMtN;
+    uint32_t idx = kMtN;
+    if (T.flags & kTileFromSlot) {
+        const uint32_t *src = (const uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.slot;
+        for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
+        idx = src[kMtN];
+        __syncwarp();
+    } else {
+        const uint32_t *src = (const uint32_t *)C.base[PRAND_MT19937];
+        bool first = true;
+        for (int b = 0; b < 64; ++b) {
+            if (!((T.stream >> b) & 1u)) continue;
+            mt_apply_poly_warp(C.mt_polys + (size_t)(kMtStreamShift + b) * kMtPolyWords, first ? src : b0, b0, b0, lane);
+            first = false;
+            __syncwarp();
+        }
+        if (first) {
+            for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
+            __syncwarp();
+        }
+    }
+    OutT *o = (OutT *)T.out;
+    const uint64_t nper = T.len;
+    uint64_t done = 0;
+    if (idx < (uint32_t)kMtN) {
+        const uint32_t cnt = (uint32_t)min((uint64_t)(kMtN - idx), nper);
+        for (uint32_t t = lane; t < cnt; t += 32) o[t] = Cvt<OutT>::f(mt_temper(b0[idx + t]));
+        done = cnt;
+        idx += cnt;
+    }
+    bool in_b0 = true;
+    while (done < nper) {
+        uint64_t rem = nper - done;
+        uint32_t emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
+        mt_twist_emit<OutT>(b0, b1, lane, o + done, emit);
+        done += emit;
+        idx = emit;
+        in_b0 = false;
+        if (done >= nper) break;
+        rem = nper - done;
+        emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
+        mt_twist_emit<OutT>(b1, b0, lane, o + done, emit);
+        done += emit;
+        idx = emit;
+        in_b0 = true;
+    }
+    if (T.flags & kTileLast) {
+        const uint32_t *cur = in_b0 ? b0 : b1;
+        uint32_t *d = (uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.wslot;
+        for (int i = lane; i < kMtN; i += 32) d[i] = cur[i];
+        if (lane == 0) d[kMtN] = idx;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ the persistent kernel
+template <typename OutT>
+__device__ __forceinline__ void batch_tile(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
+{
+    switch (T.gen) {
+    case PRAND_MT19937: batch_mt<OutT>(T, C, wsm, lane); break;
+    case PRAND_MRG32K3A: batch_mrg<OutT>(T, C, wsm, lane); break;
+    case PRAND_LFSR113: batch_lfsr<OutT>(T, C, wsm, lane); break;
+    case PRAND_GM19: batch_gm<PRAND_GM19, OutT>(T, C, wsm, lane); break;
+    case PRAND_GM29: batch_gm<PRAND_GM29, OutT>(T, C, wsm, lane); break;
+    case PRAND_GM31: batch_gm<PRAND_GM31, OutT>(T, C, wsm, lane); break;
+    case PRAND_GM55: batch_gm<PRAND_GM55, OutT>(T, C, wsm, lane); break;
+    case PRAND_GM61: batch_gm<PRAND_GM61, OutT>(T, C, wsm, lane); break;
+    case PRAND_GQ58_1: batch_gm<PRAND_GQ58_1, OutT>(T, C, wsm, lane); break;
+    case PRAND_GQ58_3: batch_gm<PRAND_GQ58_3, OutT>(T, C, wsm, lane); break;
+    default: batch_gm<PRAND_GQ58_4, OutT>(T, C, wsm, lane); break;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
+                                                              uint32_t *counter, BatchCtx ctx)
+{
+    __shared__ __align__(16) unsigned char smem[kBatchThreads / 32][kWarpSmem];
+    const int lane = threadIdx.x & 31;
+    unsigned char *wsm = smem[threadIdx.x >> 5];
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= ntiles) return;
+        const BatchTile T = tiles[t];
+        if (T.dtype == PRAND_DTYPE_U32) batch_tile<uint32_t>(T, ctx, wsm, lane);
+        else if (T.dtype == PRAND_DTYPE_F32) batch_tile<float>(T, ctx, wsm, lane);
+        else batch_tile<double>(T, ctx, wsm, lane);
+        __syncwarp();
+        if (ctx.tiles_left && lane == 0) {
+            // the request's last tile to finish publishes its completion: every
+            // tile fences its writes before counting down, the last one fences
+            // to system scope before the host-visible flag
+            __threadfence();
+            if (atomicSub(&ctx.tiles_left[T.req], 1u) == 1u) {
+                __threadfence_system();
+                ctx.req_done[T.req] = 1u;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ host: engine
+namespace {
+
+size_t esize(int dtype) { return dtype == PRAND_DTYPE_F64 ? 8 : 4; }
+
+struct SeedBases {
+    uint64_t seed = 0;
+    void *dev = nullptr;
+    size_t off[PRAND_NUM_GENERATORS] = {};
+};
+
+struct Engine {
+    int device = -1;
+    DevTables *T = nullptr;
+    std::vector<SeedBases> bases;  // small cache, most recent last
+    BatchTile *d_tiles = nullptr;
+    size_t d_cap = 0;
+    BatchTile *h_tiles = nullptr;  // pinned staging
+    size_t h_cap = 0;
+    cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
+    uint32_t *d_counter = nullptr;
+    BatchParams params;
+    int sms = 152, blocks_per_sm = 1;
+    bool ready = false;
+};
+
+constexpr int kMaxDev = 64;
+Engine g_eng[kMaxDev];
+std::mutex g_eng_mu;
+
+prand_status_t engine_get(Engine **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return PRAND_ERR_CUDA;
+    Engine &E = g_eng[dev];
+    if (!E.ready) {
+        E.device = dev;
+        prand_status_t s = get_tables(PRAND_MT19937, &E.T);
+        if (s != PRAND_OK) return s;
+        if (cudaMalloc(&E.d_counter, 64) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
+        cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev);
+        int bps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel, kBatchThreads, 0) != cudaSuccess || bps < 1)
+            bps = 1;
+        E.blocks_per_sm = bps;
+        const char *path = getenv("PRAND_TUNE_CACHE");
+        if (path) {
+            FILE *f = fopen(path, "r");
+            if (f) {
+                unsigned a = 0, b = 0;
+                if (fscanf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u", &a, &b) == 2 && a && b &&
+                    a % 4 == 0 && b % 4 == 0) {
+                    E.params.seclen_mrg_lfsr = a;
+                    E.params.seclen_gm = b;
+                }
+                fclose(f);
+            }
+        }
+        E.ready = true;
+    }
+    *out = &E;
+    return PRAND_OK;
+}
+
+// Base states of all eleven generators for one seed (computed on the device).
+prand_status_t engine_bases(Engine &E, uint64_t seed, cudaStream_t st, const SeedBases **out)
+{
+    for (size_t i = 0; i < E.bases.size(); ++i)
+        if (E.bases[i].seed == seed) { *out = &E.bases[i]; return PRAND_OK; }
+    SeedBases B;
+    B.seed = seed;
+    size_t total = 0;
+    for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) {
+        B.off[g] = total;
+        total += (state_bytes_per_stream(g) + 255) & ~(size_t)255;
+    }
+    if (cudaMalloc(&B.dev, total) != cudaSuccess) return PRAND_ERR_NOMEM;
+    prand_status_t s = PRAND_OK;
+    for (int g = 0; g < PRAND_NUM_GENERATORS && s == PRAND_OK; ++g) {
+        void *p = (char *)B.dev + B.off[g];
+        if (g == PRAND_MT19937) s = mt_seed(seed, p, st);
+        else if (is_gm(g)) s = gm_seed(g, E.T, seed, p, st);
+        else s = mrg_lfsr_seed(g, seed, p, st);
+    }
+    // wait once, so later batches on any stream see the bases
+    if (s == PRAND_OK && cudaStreamSynchronize(st) != cudaSuccess) s = PRAND_ERR_CUDA;
+    if (s != PRAND_OK) { cudaFree(B.dev); return s; }
+    if (E.bases.size() >= 4) {
+        cudaStreamSynchronize(st);
+        cudaFree(E.bases.front().dev);
+        E.bases.erase(E.bases.begin());
+    }
+    E.bases.push_back(B);
+    *out = &E.bases.back();
+    return PRAND_OK;
+}
+
+}  // namespace
+
+prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTables **T)
+{
+    Engine *E;
+    prand_status_t s = engine_get(&E);
+    if (s != PRAND_OK) return s;
+    const SeedBases *B;
+    if ((s = engine_bases(*E, seed, st, &B)) != PRAND_OK) return s;
+    memset(ctx, 0, sizeof *ctx);
+    ctx->mrg_tab = E->T->mrg;
+    ctx->lfsr_tab = E->T->lfsr;
+    ctx->mt_polys = E->T->mt;
+    for (int g = 0; g < 8; ++g) ctx->gm_tab[g] = E->T->gm[g];
+    for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) ctx->base[g] = (const char *)B->dev + B->off[g];
+    if (T) *T = E->T;
+    return PRAND_OK;
+}
+
+BatchParams batch_params()
+{
+    Engine *E;
+    if (engine_get(&E) != PRAND_OK) return BatchParams();
+    return E->params;
+}
+
+// Split one request into tiles (appended to `out`).  from_slot: continue the
+// state in `slot`; else start from the seeded base advanced to the request's
+// stream.  wslot >= 0: the request's last tile writes the next state there.
+// Section length (outputs per lane) of r's tiles: the tuned default, made
+// longer for long requests so that r yields at most max_tiles tiles (a
+// multiple of 128 outputs).
+static uint64_t section_length(const prand_request_t &r, const BatchParams &P, uint32_t max_tiles)
+{
+    const uint64_t lanes_per_tile = is_gm(r.gen) ? (uint64_t)(32 / gm_params(r.gen).lanes) : 32ull;
+    uint64_t sec = is_gm(r.gen) ? P.seclen_gm : P.seclen_mrg_lfsr;
+    if (max_tiles) {
+        const uint64_t need = (r.length + lanes_per_tile * max_tiles - 1) / (lanes_per_tile * max_tiles);
+        if (need > sec) sec = (need + 127) & ~127ull;
+    }
+    return sec;
+}
+
+uint64_t plan_tile_count(const prand_request_t &r, const BatchParams &P, uint32_t max_tiles)
+{
+    if (r.length == 0) return 0;
+    if (r.gen == PRAND_MT19937) return 1;
+    const uint64_t lanes_per_tile = is_gm(r.gen) ? (uint64_t)(32 / gm_params(r.gen).lanes) : 32ull;
+    const uint64_t per_tile = section_length(r, P, max_tiles) * lanes_per_tile;
+    return (r.length + per_tile - 1) / per_tile;
+}
+
+void plan_request(const prand_request_t &r, int32_t slot, int32_t wslot, bool from_slot, const BatchParams &P,
+                  std::vector<BatchTile> &out, uint32_t max_tiles)
+{
+    if (r.length == 0) return;
+    const int gen = r.gen;
+    const size_t es = esize(r.dtype);
+    const uintptr_t base = (uintptr_t)r.dev_out;
+    auto vec_ok = [&](uint64_t seclen) { return base % 16 == 0 && (seclen * es) % 16 == 0 && seclen % 4 == 0; };
+    const uint16_t fs = from_slot ? (uint16_t)kTileFromSlot : (uint16_t)0;
+    if (gen == PRAND_MT19937) {
+        BatchTile t = {};
+        t.stream = r.stream; t.start = 0; t.len = r.length; t.out = base;
+        t.seclen = 0; t.gen = (uint8_t)gen; t.dtype = (uint8_t)r.dtype; t.slot = slot; t.wslot = wslot;
+        t.flags = (uint16_t)(fs | (wslot >= 0 ? kTileLast : 0u));
+        out.push_back(t);
+        return;
+    }
+    const uint64_t lanes_per_tile = is_gm(gen) ? (uint64_t)(32 / gm_params(gen).lanes) : 32ull;
+    const uint64_t sec = section_length(r, P, max_tiles);
+    const uint64_t per_tile = sec * lanes_per_tile;
+    for (uint64_t off = 0; off < r.length; off += per_tile) {
+        BatchTile t = {};
+        t.stream = r.stream; t.start = off; t.len = std::min(per_tile, r.length - off);
+        t.out = base + off * es;
+        t.seclen = (uint32_t)sec; t.gen = (uint8_t)gen; t.dtype = (uint8_t)r.dtype; t.slot = slot; t.wslot = wslot;
+        t.flags = (uint16_t)(fs | (vec_ok(sec) ? kTileVec : 0u) |
+                             ((wslot >= 0 && off + t.len == r.length) ? kTileLast : 0u));
+        out.push_back(t);
+    }
+}
+
+size_t slot_words(int gen)
+{
+    if (gen == PRAND_MT19937) return kMtN + 1;
+    return state_bytes_per_stream(gen) / 4;
+}
+
+// Longest tiles first (MT19937 jump chains are the longest).
+static uint64_t tile_cost(const BatchTile &t)
+{
+    if (t.gen == PRAND_MT19937) return (1ull << 40) + t.len;
+    return t.len / (t.gen == PRAND_MRG32K3A || t.gen == PRAND_LFSR113 ? 32 : 1);
+}
+
+void order_tiles(std::vector<BatchTile> &tiles)
+{
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const BatchTile &a, const BatchTile &b) { return tile_cost(a) > tile_cost(b); });
+}
+
+prand_status_t validate_requests(const prand_request_t *reqs, size_t n)
+{
+    if (!reqs && n) return PRAND_ERR_ARG;
+    for (size_t i = 0; i < n; ++i) {
+        const prand_request_t &r = reqs[i];
+        if (r.gen < 0 || r.gen >= PRAND_NUM_GENERATORS || r.dtype < 0 || r.dtype > 2) return PRAND_ERR_ARG;
+        if (r.length && !r.dev_out) return PRAND_ERR_ARG;
+        if ((uintptr_t)r.dev_out % esize(r.dtype)) return PRAND_ERR_ALIGN;
+        uint64_t bytes;
+        if (__builtin_mul_overflow(r.length, (uint64_t)esize(r.dtype), &bytes)) return PRAND_ERR_ARG;
+    }
+    return PRAND_OK;
+}
+
+unsigned batch_grid(uint32_t ntiles)
+{
+    Engine *E;
+    if (engine_get(&E) != PRAND_OK) return 1;
+    uint64_t warps_needed = ntiles, per_block = kBatchThreads / 32;
+    uint64_t g = std::min<uint64_t>((warps_needed + per_block - 1) / per_block, (uint64_t)E->sms * E->blocks_per_sm);
+    return (unsigned)std::max<uint64_t>(g, 1);
+}
+
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t *d_counter, const BatchCtx &ctx,
+                            cudaStream_t st)
+{
+    if (cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
+    if (!ntiles) return PRAND_OK;
+    batch_kernel<<<batch_grid(ntiles), kBatchThreads, 0, st>>>(d_tiles, ntiles, d_counter, ctx);
+    return launch_check();
+}
+
+// Tiles to the device through the engine's pinned staging buffer.
+prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter)
+{
+    Engine *E;
+    prand_status_t s = engine_get(&E);
+    if (s != PRAND_OK) return s;
+    const size_t n = tiles.size();
+    if (cudaEventSynchronize(E->staged) != cudaSuccess) return PRAND_ERR_CUDA;  // staging free again
+    if (n > E->h_cap) {
+        if (E->h_tiles) cudaFreeHost(E->h_tiles);
+        E->h_cap = std::max<size_t>(n, 2 * E->h_cap);
+        if (cudaMallocHost(&E->h_tiles, E->h_cap * sizeof(BatchTile)) != cudaSuccess) { E->h_cap = 0; E->h_tiles = nullptr; return PRAND_ERR_NOMEM; }
+    }
+    if (n > E->d_cap) {
+        // the previous batch may still read the old buffer: free it in stream order
+        if (E->d_tiles) { cudaStreamSynchronize(st); cudaFree(E->d_tiles); }
+        E->d_cap = std::max<size_t>(n, 2 * E->d_cap);
+        if (cudaMalloc(&E->d_tiles, E->d_cap * sizeof(BatchTile)) != cudaSuccess) { E->d_cap = 0; E->d_tiles = nullptr; return PRAND_ERR_NOMEM; }
+    }
+    if (n) {
+        memcpy(E->h_tiles, tiles.data(), n * sizeof(BatchTile));
+        if (cudaMemcpyAsync(E->d_tiles, E->h_tiles, n * sizeof(BatchTile), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return PRAND_ERR_CUDA;
+        if (cudaEventRecord(E->staged, st) != cudaSuccess) return PRAND_ERR_CUDA;
+    }
+    *d_out = E->d_tiles;
+    *counter = E->d_counter;
+    return PRAND_OK;
+}
+
+}  // namespace prand
+
+using namespace prand;
+
+// ------------------------------------------------------------------ C ABI
+struct prand_batch_plan_s {
+    int device = -1;
+    BatchTile *d_tiles = nullptr;
+    uint32_t ntiles = 0;
+    uint32_t *d_counter = nullptr;
+    BatchCtx ctx;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream)
+{
+    prand_status_t s = validate_requests(reqs, n);
+    if (s != PRAND_OK || n == 0) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchCtx ctx;
+    if ((s = batch_ctx(seed, st, &ctx, nullptr)) != PRAND_OK) return s;
+    const BatchParams P = batch_params();
+    std::vector<BatchTile> tiles;
+    tiles.reserve(n * 2);
+    for (size_t i = 0; i < n; ++i) plan_request(reqs[i], -1, -1, false, P, tiles);
+    order_tiles(tiles);
+    if (tiles.size() > 0xFFFFFFFFull) return PRAND_ERR_ARG;
+    BatchTile *d_tiles;
+    uint32_t *counter;
+    if ((s = upload_tiles(tiles, st, &d_tiles, &counter)) != PRAND_OK) return s;
+    return launch_batch(d_tiles, (uint32_t)tiles.size(), counter, ctx, st);
+}
+
+prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_request_t *reqs, size_t n, uint64_t seed)
+{
+    if (!out) return PRAND_ERR_ARG;
+    *out = nullptr;
+    prand_status_t s = validate_requests(reqs, n);
+    if (s != PRAND_OK) return s;
+    prand_batch_plan_t p = new (std::nothrow) prand_batch_plan_s;
+    if (!p) return PRAND_ERR_NOMEM;
+    cudaGetDevice(&p->device);
+    cudaStream_t cap = nullptr;
+    auto fail = [&](prand_status_t e) {
+        if (cap) cudaStreamDestroy(cap);
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        if (p->d_tiles) cudaFree(p->d_tiles);
+        if (p->d_counter) cudaFree(p->d_counter);
+        delete p;
+        return e;
+    };
+    if ((s = batch_ctx(seed, 0, &p->ctx, nullptr)) != PRAND_OK) return fail(s);
+    const BatchParams P = batch_params();
+    std::vector<BatchTile> tiles;
+    for (size_t i = 0; i < n; ++i) plan_request(reqs[i], -1, -1, false, P, tiles);
+    order_tiles(tiles);
+    if (tiles.size() > 0xFFFFFFFFull) return fail(PRAND_ERR_ARG);
+    p->ntiles = (uint32_t)tiles.size();
+    if (cudaMalloc(&p->d_counter, 64) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+    if (p->ntiles) {
+        if (cudaMalloc(&p->d_tiles, tiles.size() * sizeof(BatchTile)) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+        if (cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(PRAND_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
+    // capture: counter reset + the persistent launch
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(PRAND_ERR_CUDA);
+    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->d_counter, p->ctx, cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    p->graph = g;
+    if (ls != PRAND_OK || ce != cudaSuccess) return fail(PRAND_ERR_CUDA);
+    if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
+    cudaStreamDestroy(cap);
+    cap = nullptr;
+    *out = p;
+    return PRAND_OK;
+}
+
+prand_status_t prand_batch_plan_launch(prand_batch_plan_t p, prand_stream_t stream)
+{
+    if (!p || !p->exec) return PRAND_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return PRAND_ERR_STATE;
+    g_launches.fetch_add(p->ntiles ? 1 : 0, std::memory_order_relaxed);
+    return cudaGraphLaunch(p->exec, (cudaStream_t)stream) == cudaSuccess ? PRAND_OK : PRAND_ERR_CUDA;
+}
+
+prand_status_t prand_batch_plan_destroy(prand_batch_plan_t p)
+{
+    if (!p) return PRAND_OK;
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_tiles) cudaFree(p->d_tiles);
+    if (p->d_counter) cudaFree(p->d_counter);
+    delete p;
+    return PRAND_OK;
+}
+
+prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream,
+                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, float *best_ms)
+{
+    prand_status_t s = validate_requests(reqs, n);
+    if (s != PRAND_OK) return s;
+    Engine *E;
+    if ((s = engine_get(&E)) != PRAND_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t cand[] = { 2048, 8192, 32768 };
+    const BatchParams keep = E->params;
+    BatchParams best = keep;
+    float best_t = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (uint32_t a : cand)
+        for (uint32_t b : cand) {
+            E->params.seclen_mrg_lfsr = a;
+            E->params.seclen_gm = b;
+            prand_batch_plan_t plan;
+            if ((s = prand_batch_plan_create(&plan, reqs, n, seed)) != PRAND_OK) break;
+            prand_batch_plan_launch(plan, stream);  // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) prand_batch_plan_launch(plan, stream);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3;
+            prand_batch_plan_destroy(plan);
+            if (ms < best_t) { best_t = ms; best = E->params; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    E->params = s == PRAND_OK ? best : keep;
+    if (s != PRAND_OK) return s;
+    if (seclen_mrg_lfsr) *seclen_mrg_lfsr = best.seclen_mrg_lfsr;
+    if (seclen_gm) *seclen_gm = best.seclen_gm;
+    if (best_ms) *best_ms = best_t;
+    const char *path = getenv("PRAND_TUNE_CACHE");
+    if (path) {
+        FILE *f = fopen(path, "w");
+        if (f) {
+            fprintf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u, \"ms\": %.4f}\n", best.seclen_mrg_lfsr,
+                    best.seclen_gm, best_t);
+            fclose(f);
+        }
+    }
+    return PRAND_OK;
+}
+
+// Per-request plain launches (for comparison with the fused form): for every
+// request, the ordinary stream-initialisation launch(es) and generation launch
+// on one stream, with no fusion and no persistent scheduling.
+prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream)
+{
+    prand_status_t s = validate_requests(reqs, n);
+    if (s != PRAND_OK || n == 0) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchCtx ctx;
+    DevTables *T;
+    if ((s = batch_ctx(seed, st, &ctx, &T)) != PRAND_OK) return s;
+    size_t maxb = 0;
+    for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) maxb = std::max(maxb, state_bytes_per_stream(g));
+    void *scratch = nullptr;
+    if (n && cudaMalloc(&scratch, 2 * maxb * n) != cudaSuccess) return PRAND_ERR_NOMEM;
+    for (size_t i = 0; i < n && s == PRAND_OK; ++i) {
+        const prand_request_t &r = reqs[i];
+        if (!r.length) continue;
+        void *a = (char *)scratch + 2 * maxb * i, *b = (char *)a + maxb;
+        bool sw = false;
+        uint32_t idx = kMtN;
+        if (r.gen == PRAND_MT19937) {
+            s = mt_init(T, ctx.base[r.gen], a, r.stream, 1, st);
+            if (s == PRAND_OK) s = mt_gen(a, 1, &idx, r.dev_out, r.dtype, r.length, st);
+        } else if (is_gm(r.gen)) {
+            s = gm_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
+            if (s == PRAND_OK) s = gm_gen(r.gen, T, a, b, 1, r.dev_out, r.dtype, r.length, st, &sw);
+        } else {
+            s = mrg_lfsr_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
+            if (s == PRAND_OK) s = mrg_lfsr_gen(r.gen, T, a, b, 1, r.dev_out, r.dtype, r.length, st, &sw);
+        }
+    }
+    // scratch is freed in stream order (the runtime defers it until the work is done)
+    cudaStreamSynchronize(st);
+    if (scratch) cudaFree(scratch);
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Shared declarations of the batched persistent kernel (batch.cu) and the
+// resident-stream server built on it (serve.cpp).
+#pragma once
+
+#include <vector>
+
+#include "prand_internal.h"
+
+namespace prand {
+
+constexpr uint32_t kTileLast = 1u;      // the tile holds the request's last output: write the next state to wslot
+constexpr uint32_t kTileVec = 2u;       // every row start is 16-byte aligned: vector / staged-row stores
+constexpr uint32_t kTileFromSlot = 4u;  // start from the state in slot (else from the seeded base + stream * L)
+
+// One unit of work for one warp (64 bytes).
+struct BatchTile {
+    uint64_t stream;  // stream index k (block splitting: base advanced by k L)
+    uint64_t start;   // offset of the tile's first output inside the request
+    uint64_t len;     // outputs in the tile
+    uint64_t out;     // device address of the tile's first output
+    uint32_t seclen;  // outputs per lane (MRG32K3A, LFSR113) or per lane group (GM/GQ)
+    int32_t slot;     // state slot read with kTileFromSlot
+    int32_t wslot;    // state slot written with kTileLast (a different buffer than slot)
+    uint8_t gen, dtype;
+    uint16_t flags;
+    uint32_t req;     // index of the tile's request in its batch (completion tracking)
+    uint32_t pad_[3];
+};
+static_assert(sizeof(BatchTile) == 64, "tile layout");
+
+struct BatchCtx {
+    const uint32_t *mrg_tab, *lfsr_tab, *mt_polys;
+    const uint64_t *gm_tab[8];
+    const void *base[PRAND_NUM_GENERATORS];  // base states of the batch's seed
+    void *slots[PRAND_NUM_GENERATORS];       // resident-state arenas (server)
+    uint32_t *tiles_left;                    // per request: tiles not finished (server), or null
+    volatile uint32_t *req_done;             // per request: set to 1 in mapped host memory when done
+};
+
+struct BatchParams {
+    uint32_t seclen_mrg_lfsr = 8192;  // outputs per section, chosen by the tuner
+    uint32_t seclen_gm = 8192;
+};
+
+prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTables **T);
+BatchParams batch_params();
+void plan_request(const prand_request_t &r, int32_t slot, int32_t wslot, bool from_slot, const BatchParams &P,
+                  std::vector<BatchTile> &out, uint32_t max_tiles = 0);
+// Number of tiles plan_request() makes for r (without planning it).
+uint64_t plan_tile_count(const prand_request_t &r, const BatchParams &P, uint32_t max_tiles = 0);
+size_t slot_words(int gen);  // 32-bit words per state slot
+prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter);
+void order_tiles(std::vector<BatchTile> &tiles);
+prand_status_t validate_requests(const prand_request_t *reqs, size_t n);
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t *d_counter, const BatchCtx &ctx,
+                            cudaStream_t st);
+
+}  // namespace prand

@@ -352,30 +352,4 @@ const char *prand_status_string(prand_status_t s)
 
 uint64_t prand_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream)
-{
-    // Reference form of the batch: one handle per request, each request its own
-    // launches.  (The fused persistent form replaces this body.)
-    if (!reqs && n) return PRAND_ERR_ARG;
-    for (size_t i = 0; i < n; ++i) {
-        const prand_request_t &r = reqs[i];
-        if (r.gen < 0 || r.gen >= PRAND_NUM_GENERATORS || r.dtype < 0 || r.dtype > 2 || (!r.dev_out && r.length))
-            return PRAND_ERR_ARG;
-    }
-    for (size_t i = 0; i < n; ++i) {
-        const prand_request_t &r = reqs[i];
-        if (!r.length) continue;
-        prand_handle_t h;
-        prand_status_t s = prand_create(&h, (prand_gen_t)r.gen, seed);
-        if (s != PRAND_OK) return s;
-        s = prand_init_streams(h, r.stream, 1);
-        if (s != PRAND_OK && s != PRAND_WARN_STREAM_OVERLAP) { prand_destroy(h); return s; }
-        s = generate_any(h, r.dev_out, r.dtype, r.length, stream);
-        if (s == PRAND_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = PRAND_ERR_CUDA;
-        prand_destroy(h);
-        if (s != PRAND_OK) return s;
-    }
-    return PRAND_OK;
-}
-
 }  // extern "C"

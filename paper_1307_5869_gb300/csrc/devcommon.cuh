@@ -201,13 +201,24 @@ __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, ui
     unsigned char *myrow = tile + lane * kTilePitch;
     for (uint64_t ch = 0; ch < nch; ++ch) {
         const uint32_t cnt = len > ch * K ? (uint32_t)min((uint64_t)K, len - ch * K) : 0u;
+        if (__all_sync(kFull, cnt == (uint32_t)K)) {
+            // every lane has a whole chunk: no per-output tests
 #pragma unroll
-        for (int v = 0; v < K / E; ++v) {
-            if ((uint32_t)(v * E) < cnt) {
+            for (int v = 0; v < K / E; ++v) {
                 OutT vals[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) vals[e] = (uint32_t)(v * E + e) < cnt ? cvt(next()) : OutT(0);
+                for (int e = 0; e < E; ++e) vals[e] = cvt(next());
                 *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < K / E; ++v) {
+                if ((uint32_t)(v * E) < cnt) {
+                    OutT vals[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) vals[e] = (uint32_t)(v * E + e) < cnt ? cvt(next()) : OutT(0);
+                    *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
+                }
             }
         }
         __syncwarp();

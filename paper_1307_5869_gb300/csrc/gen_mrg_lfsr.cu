@@ -7,46 +7,11 @@
 // GF(2) powers of the LFSR word step), exactly as the paper's array fill
 // splits an array into sections (Sec. 6).  State is stored structure-of-arrays
 // (word c of stream j at state[c * nstreams + j]) so a warp loads it coalesced.
-#include "devcommon.cuh"
+#include "mrg_lfsr_dev.cuh"
 
 namespace prand {
 
 // =========================================================== MRG32K3A
-// Matrices of Sec. 5.2 with the negative entries taken mod m.
-__device__ __forceinline__ void mrg_step_matrices(uint32_t A[9], uint32_t B[9])
-{
-    const uint32_t a0[9] = { 0u, 1403580u, kM1 - 810728u, 1u, 0u, 0u, 0u, 1u, 0u };
-    const uint32_t b0[9] = { 527612u, 0u, kM2 - 1370589u, 1u, 0u, 0u, 0u, 1u, 0u };
-    for (int i = 0; i < 9; ++i) { A[i] = a0[i]; B[i] = b0[i]; }
-}
-
-template <uint32_t C>
-__device__ void mat3_sqr(uint32_t M[9])
-{
-    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
-    uint32_t R[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            uint32_t s = 0;
-            for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], M[3 * k + j]), m);
-            R[3 * i + j] = s;
-        }
-    for (int i = 0; i < 9; ++i) M[i] = R[i];
-}
-
-template <uint32_t C>
-__device__ __forceinline__ void mat3_vec(const uint32_t *M, uint32_t v[3])
-{
-    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
-    uint32_t r[3];
-    for (int i = 0; i < 3; ++i) {
-        uint32_t s = 0;
-        for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], v[k]), m);
-        r[i] = s;
-    }
-    v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
-}
-
 // tab[b] = (A^(2^b) mod m1, B^(2^b) mod m2), b < kJumpBits.
 __global__ void mrg_table_kernel(uint32_t *tab)
 {
@@ -58,13 +23,6 @@ __global__ void mrg_table_kernel(uint32_t *tab)
         mat3_sqr<209>(A);
         mat3_sqr<22853>(B);
     }
-}
-
-// Apply the jump of bit b of the table to (x, y).
-__device__ __forceinline__ void mrg_apply_bit(const uint32_t *tab, int b, uint32_t x[3], uint32_t y[3])
-{
-    mat3_vec<209>(tab + 18 * b, x);
-    mat3_vec<22853>(tab + 18 * b + 9, y);
 }
 
 // Default state: all six words 12345 (the paper does not print it; L'Ecuyer's
@@ -104,25 +62,6 @@ __global__ void mrg_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t n
     for (int b = 0; b < kJumpBits; ++b)
         if (u256_bit(off, b)) mrg_apply_bit(tab, b, x, y);
     for (int i = 0; i < 3; ++i) { state[i * n + j] = x[i]; state[(3 + i) * n + j] = y[i]; }
-}
-
-// One step of both components and the output z = (x - y) mod m1 in [1, m1].
-// x_{n+1} = 1403580 x_{n-1} - 810728 x_{n-2} (mod m1)
-// y_{n+1} = 527612 y_n - 1370589 y_{n-2}     (mod m2)
-__device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_t &x2,
-                                             uint32_t &y0, uint32_t &y1, uint32_t &y2)
-{
-    // signed difference of two < 2^53 products, shifted positive by a multiple of m
-    uint64_t u = (uint64_t)1403580u * x1 + (uint64_t)810728u * (uint64_t)kM1 - (uint64_t)810728u * x2;  // < 2^54
-    uint64_t r = (u & 0xFFFFFFFFull) + 209ull * (u >> 32);                                                 // < 2^32 + 2^30
-    uint32_t xn = (uint32_t)(r >= kM1 ? r - kM1 : r);
-    uint64_t w = (uint64_t)527612u * y0 + (uint64_t)1370589u * (uint64_t)kM2 - (uint64_t)1370589u * y2;   // < 2^54
-    uint64_t s = (w & 0xFFFFFFFFull) + 22853ull * (w >> 32);                                               // < 2^32 + 2^37
-    s = (s & 0xFFFFFFFFull) + 22853ull * (s >> 32);                                                        // < 2^32 + 2^20
-    uint32_t yn = (uint32_t)(s >= kM2 ? s - kM2 : s);
-    x2 = x1; x1 = x0; x0 = xn;
-    y2 = y1; y1 = y0; y0 = yn;
-    return xn > yn ? xn - yn : xn - yn + kM1;
 }
 
 // One thread = one section of one stream.  Sections have length seclen (the
@@ -194,34 +133,6 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
 }
 
 // =========================================================== LFSR113
-// Component (p, q, s): (31,6,18), (29,2,2), (28,13,7), (25,3,13).  The word
-// holds bits x_{ns}..x_{ns+31} of eq. (lfsrOutput); a step keeps the top p bits
-// shifted by s and refills the rest through eq. (lfsrRel1).
-template <int P, int Q, int S>
-__host__ __device__ __forceinline__ uint32_t taus_step(uint32_t z)
-{
-    constexpr uint32_t mask = 0xFFFFFFFFu << (32 - P);
-    return ((z & mask) << S) ^ (((z << Q) ^ z) >> (P - S));
-}
-
-__device__ __forceinline__ uint32_t lfsr_comp_step(int c, uint32_t z)
-{
-    switch (c) {
-    case 0: return taus_step<31, 6, 18>(z);
-    case 1: return taus_step<29, 2, 2>(z);
-    case 2: return taus_step<28, 13, 7>(z);
-    default: return taus_step<25, 3, 13>(z);
-    }
-}
-
-__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *col, uint32_t v)
-{
-    uint32_t r = 0;
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) r ^= ((v >> i) & 1u) ? col[i] : 0u;
-    return r;
-}
-
 // tab[(c * kJumpBits + b) * 32 + i] = image of bit i under the word step of
 // component c applied 2^b times.  One thread per component.
 __global__ void lfsr_table_kernel(uint32_t *tab)
@@ -235,11 +146,6 @@ __global__ void lfsr_table_kernel(uint32_t *tab)
         for (int i = 0; i < 32; ++i) sq[i] = gf2_apply(col, col[i]);
         for (int i = 0; i < 32; ++i) col[i] = sq[i];
     }
-}
-
-__device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint32_t z[4])
-{
-    for (int c = 0; c < 4; ++c) z[c] = gf2_apply(tab + ((size_t)c * kJumpBits + b) * 32, z[c]);
 }
 
 // Default state: 987654321 in all four words (L'Ecuyer's example seed; the paper
@@ -281,15 +187,6 @@ __global__ void lfsr_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t 
     for (int b = 0; b < kJumpBits; ++b)
         if (u256_bit(off, b)) lfsr_apply_bit(tab, b, z);
     for (int c = 0; c < 4; ++c) state[c * n + j] = z[c];
-}
-
-__device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)
-{
-    z0 = taus_step<31, 6, 18>(z0);
-    z1 = taus_step<29, 2, 2>(z1);
-    z2 = taus_step<28, 13, 7>(z2);
-    z3 = taus_step<25, 3, 13>(z3);
-    return z0 ^ z1 ^ z2 ^ z3;
 }
 
 template <typename OutT, bool ROWS = false>

@@ -6,8 +6,8 @@
 // x_{t+624} = x_{t+397} ^ twist(x_t^u | x_{t+1}^l): words 0..226 read only old
 // words, words 227..453 read words 0..226 of the new block, words 454..623 read
 // words 227..396 of the new block (Table 5 uses 227 threads per stream for the
-// same reason).  Output words leave tempered, 32 consecutive words per store
-// instruction.
+// same reason).  Each new word leaves tempered straight from registers, 32
+// consecutive words per store instruction.
 //
 // State layout: stream j at state[j * 624 .. j * 624 + 623].  All streams of a
 // handle share the position inside the current block (the handle's index), so
@@ -17,26 +17,11 @@
 // With Y in window form (x_t..x_{t+623}), A^i Y is the window starting at
 // x_{t+i}, so the sum is a sliding-window XOR over the stream's next 20560
 // words, taken at the set coefficients of g_v.
-#include "devcommon.cuh"
+#include "mt_dev.cuh"
 
 namespace prand {
 
 constexpr int kMtWarpsPerBlock = 4;
-
-__device__ __forceinline__ uint32_t mt_recur(uint32_t xt, uint32_t xt1, uint32_t xt397)
-{
-    uint32_t y = (xt & 0x80000000u) | (xt1 & 0x7FFFFFFFu);
-    return xt397 ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
-}
-
-__device__ __forceinline__ uint32_t mt_temper(uint32_t y)
-{
-    y ^= y >> 11;
-    y ^= (y << 7) & 0x9D2C5680u;
-    y ^= (y << 15) & 0xEFC60000u;
-    y ^= y >> 18;
-    return y;
-}
 
 // ------------------------------------------------------------------ seeding
 // seed < 2^32: init_genrand(seed); wider seeds: init_by_array({lo32, hi32});
@@ -67,132 +52,49 @@ __global__ void mt_seed_kernel(uint32_t *base, uint64_t seed)
     base[0] = 0x80000000u;
 }
 
-// ------------------------------------------------------------------ twist
-// In-place twist of a 624-word block in shared memory by one warp.
-__device__ __forceinline__ void mt_twist_warp(uint32_t *mt, int lane)
-{
-    // phase 1: k in [0, 227) reads mt[k+397] (old)
-    // phase 2: k in [227, 454) reads mt[k-227] (new, phase 1)
-    // phase 3: k in [454, 624) reads mt[k-227] (new, phase 2); k = 623 reads mt[0] (new)
-    const int lo[3] = { 0, 227, 454 }, hi[3] = { 227, 454, 624 };
-#pragma unroll
-    for (int ph = 0; ph < 3; ++ph) {
-        for (int k0 = lo[ph]; k0 < hi[ph]; k0 += 32) {
-            int k = k0 + lane;
-            bool act = k < hi[ph];
-            uint32_t a = 0, b = 0, c = 0;
-            if (act) {
-                a = mt[k];
-                b = mt[k + 1 < kMtN ? k + 1 : 0];
-                c = mt[k < 227 ? k + 397 : k - 227];
-            }
-            __syncwarp();
-            if (act) mt[k] = mt_recur(a, b, c);
-            __syncwarp();
-        }
-    }
-}
-
 // ------------------------------------------------------------------ generation
 template <typename OutT>
 __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_gen_kernel(uint32_t *state, uint64_t nstreams, uint32_t idx0,
                                                                        uint64_t nper, OutT *__restrict__ out)
 {
-    __shared__ uint32_t sm[kMtWarpsPerBlock][kMtN];
+    __shared__ uint32_t sm[kMtWarpsPerBlock][2][kMtN];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
     if (j >= nstreams) return;  // whole warp
-    uint32_t *mt = sm[w];
+    uint32_t *b0 = sm[w][0], *b1 = sm[w][1];
     const uint32_t *src = state + j * kMtN;
-    for (int i = lane; i < kMtN; i += 32) mt[i] = src[i];
+    for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
     __syncwarp();
-    uint32_t idx = idx0;
-    uint64_t done = 0;
     OutT *o = out + j * nper;
-    while (done < nper) {
-        if (idx >= (uint32_t)kMtN) { mt_twist_warp(mt, lane); idx = 0; }
-        uint64_t cnt = min((uint64_t)(kMtN - idx), nper - done);
-        for (uint64_t t = lane; t < cnt; t += 32) o[done + t] = Cvt<OutT>::f(mt_temper(mt[idx + t]));
-        idx += (uint32_t)cnt;
-        done += cnt;
+    uint64_t done = 0;
+    // the rest of the current block
+    if (idx0 < (uint32_t)kMtN) {
+        const uint32_t cnt = (uint32_t)min((uint64_t)(kMtN - idx0), nper);
+        for (uint32_t t = lane; t < cnt; t += 32) o[t] = Cvt<OutT>::f(mt_temper(b0[idx0 + t]));
+        done = cnt;
     }
-    __syncwarp();
+    // whole new blocks, each twisted once and emitted as it is made; the loop
+    // is unrolled by two so both calls see fixed shared-memory buffers
+    bool in_b0 = true;
+    while (done < nper) {
+        uint64_t rem = nper - done;
+        uint32_t emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
+        mt_twist_emit<OutT>(b0, b1, lane, o + done, emit);
+        done += emit;
+        in_b0 = false;
+        if (done >= nper) break;
+        rem = nper - done;
+        emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
+        mt_twist_emit<OutT>(b1, b0, lane, o + done, emit);
+        done += emit;
+        in_b0 = true;
+    }
+    const uint32_t *cur = in_b0 ? b0 : b1;
     uint32_t *dst = state + j * kMtN;
-    for (int i = lane; i < kMtN; i += 32) dst[i] = mt[i];
+    for (int i = lane; i < kMtN; i += 32) dst[i] = cur[i];
 }
 
 // ------------------------------------------------------------------ jump
-// dst := g(A) src for one stream, by one warp.  seq is a 1248-word ring in
-// shared memory holding two consecutive 624-word blocks of the stream.
-// acc[r] accumulates result word m = lane + 32 r (m < 624).
-__device__ void mt_apply_poly_warp(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst, uint32_t *seq,
-                                   int lane)
-{
-    constexpr int R = (kMtN + 31) / 32;  // 20
-    uint32_t acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0;
-    for (int i = lane; i < kMtN; i += 32) seq[i] = src[i];
-    __syncwarp();
-    // block 1 = words 624..1247 of the stream, into slot 1
-    auto twist_into = [&](int out_slot) {
-        // x_T = recur(x_{T-624}, x_{T-623}, x_{T-227}) for T in the new block;
-        // the previous block sits in the other slot.
-        uint32_t *nb = seq + out_slot * kMtN;
-        const uint32_t *ob = seq + (out_slot ^ 1) * kMtN;
-        const int lo[3] = { 0, 227, 454 }, hi[3] = { 227, 454, 624 };
-#pragma unroll
-        for (int ph = 0; ph < 3; ++ph) {
-            for (int k = lo[ph] + lane; k < hi[ph]; k += 32) {
-                uint32_t a = ob[k];
-                uint32_t b = (k + 1 < kMtN) ? ob[k + 1] : nb[0];
-                uint32_t c = (k < 227) ? ob[k + 397] : nb[k - 227];
-                nb[k] = mt_recur(a, b, c);
-            }
-            __syncwarp();
-        }
-    };
-    twist_into(1);
-    // coefficient i of g (i < 19937) selects the window starting at x_i.
-    for (int B = 0; B * kMtN < kMtDeg; ++B) {
-        const int base_slot = B & 1;
-        const int i_lo = B * kMtN, i_hi = min(i_lo + kMtN, kMtDeg);
-        for (int wd = i_lo >> 5; (wd << 5) < i_hi; ++wd) {
-            uint32_t bits = __ldg(poly + wd);
-            // keep the bits of this word that fall in [i_lo, i_hi)
-            int b0 = (wd << 5);
-            if (b0 < i_lo) bits &= 0xFFFFFFFFu << (i_lo - b0);
-            if (b0 + 32 > i_hi) bits &= (i_hi - b0) >= 32 ? 0xFFFFFFFFu : ((1u << (i_hi - b0)) - 1u);
-            while (bits) {
-                int bb = __ffs(bits) - 1;
-                bits &= bits - 1;
-                int d = b0 + bb - i_lo;                  // offset of x_i inside block B
-                int p0 = base_slot * kMtN + d;           // ring position of x_i
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    int m = lane + 32 * r;
-                    if (m < kMtN) {
-                        int p = p0 + m;
-                        if (p >= 2 * kMtN) p -= 2 * kMtN;
-                        acc[r] ^= seq[p];
-                    }
-                }
-            }
-        }
-        // the window of the next block needs block B + 2 in slot (B & 1)
-        if ((B + 1) * kMtN < kMtDeg) {
-            __syncwarp();
-            twist_into(base_slot);
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int m = lane + 32 * r;
-        if (m < kMtN) dst[m] = acc[r];
-    }
-}
-
 // Doubling level: dst stream (off + j) := g(A) (src stream j), j < count.
 __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_level_kernel(const uint32_t *poly, uint32_t *state,
                                                                          uint64_t off, uint64_t count)

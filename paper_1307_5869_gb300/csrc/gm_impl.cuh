@@ -97,20 +97,36 @@ __device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t zc, uint64_t zp
     uint64_t h = S >> 51;                                  // < 2^10
     return S - h * p;                                      // (S mod 2^51) + 129 h < 2^51 + 2^18
 }
-// p = 2^61 - 1; lazy z < 2^61 + 256.  Limbs of 32 bits: four 32x32->64
-// multiply-adds give S = 24 z + 74 (2p - y) < 2^69 as (B, A.lo).
+// p = 2^61 - 1; lazy z < 2^61 + 256.  32-bit limbs: with t = 2p - y,
+// A = 24 z0 + 74 t0 and B = 24 z1 + 74 t1 + A.hi (four 32x32->64 multiply-adds)
+// give S = 24 z + 74 t = A.lo + 2^32 B < 2^69.  With h = S >> 61 = B >> 29 and
+// m = B mod 2^29 = b0 - h 2^29, the fold is R = A.lo + h + 2^32 m.
 template <>
 __device__ __forceinline__ uint64_t gm_step<PRAND_GM61>(uint64_t zc, uint64_t zp)
 {
-    const uint64_t t = 0x3FFFFFFFFFFFFFFEull - zp;        // 2p - y, (0, 2^62)
     const uint32_t z0 = (uint32_t)zc, z1 = (uint32_t)(zc >> 32);
-    const uint32_t t0 = (uint32_t)t, t1 = (uint32_t)(t >> 32);
-    const uint64_t A = (uint64_t)z0 * 24u + (uint64_t)t0 * 74u;
-    const uint64_t B = (uint64_t)z1 * 24u + (uint64_t)t1 * 74u + (A >> 32);
-    const uint32_t b0 = (uint32_t)B, b1 = (uint32_t)(B >> 32);
-    const uint32_t h = __funnelshift_r(b0, b1, 29);        // S >> 61 (< 2^8)
-    uint64_t R = (((uint64_t)b0 << 32) | (uint32_t)A) + h; // low 64 bits of S, plus h
-    return R - ((uint64_t)h << 61);                        // (S mod 2^61) + h < 2^61 + 256
+    const uint32_t y0 = (uint32_t)zp, y1 = (uint32_t)(zp >> 32);
+    uint32_t r0, r1;
+    asm("{\n\t"
+        ".reg .u32 t0, t1, a0, a1, b0, b1, h, m;\n\t"
+        ".reg .u64 A, B, T;\n\t"
+        "sub.cc.u32 t0, 0xFFFFFFFE, %2;\n\t"
+        "subc.u32 t1, 0x3FFFFFFF, %3;\n\t"
+        "mul.wide.u32 T, t0, 74;\n\t"
+        "mad.wide.u32 A, %4, 24, T;\n\t"
+        "mov.b64 {a0, a1}, A;\n\t"
+        "cvt.u64.u32 T, a1;\n\t"
+        "mad.wide.u32 T, t1, 74, T;\n\t"
+        "mad.wide.u32 B, %5, 24, T;\n\t"
+        "mov.b64 {b0, b1}, B;\n\t"
+        "shf.r.wrap.b32 h, b0, b1, 29;\n\t"
+        "mad.lo.u32 m, h, 0xE0000000, b0;\n\t"
+        "add.cc.u32 %0, a0, h;\n\t"
+        "addc.u32 %1, m, 0;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1)
+        : "r"(y0), "r"(y1), "r"(z0), "r"(z1));
+    return ((uint64_t)r1 << 32) | r0;
 }
 // p = 2^29 - 3 (GQ58.x, z = x / 2^29); lazy z < 2^29 + 384
 template <>
@@ -135,8 +151,8 @@ __device__ __forceinline__ bool gm_strip1(uint64_t z)  // v = 1: canonical z in 
 {
     using P = GmT<GEN>;
     if (P::kind == P61) {
-        // z < 2^61 + 256: bit 60 set and z != p  <=>  canonical z >= 2^60
-        return ((uint32_t)(z >> 32) & 0x10000000u) && z != P::p;
+        // z < 2^61 + 256: canonical z >= 2^60  <=>  2^60 <= z < p
+        return z - (1ull << 60) <= (1ull << 60) - 2;
     }
     constexpr uint32_t half = (uint32_t)((P::p + 1) / 2);
     return (uint32_t)z - half < (uint32_t)(P::p - half);
@@ -279,57 +295,38 @@ __device__ __forceinline__ uint32_t gm_next_word(uint64_t &zc, uint64_t &zp, boo
     return __reduce_or_sync(gmask, w);
 }
 
-// One group = one section of one stream.  A round makes 4 * lanes words; lane
-// li keeps words 4 li .. 4 li + 3 of the round and stores them together, so a
-// group writes 16 * lanes contiguous bytes per round.  Full rounds run without
-// bounds checks; the last, partial round steps exactly the remaining count.
-// Every point takes exactly `len` steps, so the group of the last section holds
-// the stream's next state and writes it to state_out (a separate buffer when a
-// stream is split into several sections, so no group reads a state another
-// group has already replaced).
-// VEC (chosen on the host) means every row start is 16-byte aligned, so full
-// rounds leave as one 16-byte store per lane; otherwise as 4-byte stores.  The
-// two forms are separate kernels: a run-time branch between two stores of the
-// same values to the same addresses may be folded into the wider one.
+// One group generates `len` outputs of one section into o: rounds of 4 * lanes
+// words; lane li keeps words 4 li .. 4 li + 3 of a round and stores them
+// together, so a group writes 16 * lanes contiguous bytes per round.  The lane
+// that owns words 4c..4c+3 parks them in its own 16-byte shared-memory slot (a
+// predicated store instead of four register selects).  Full rounds run without
+// bounds checks; the last, partial round steps exactly the remaining count, so
+// every point takes exactly `len` steps.  VEC: o is 16-byte aligned (32 for
+// doubles) at every round start, so full rounds leave as one vector store per
+// lane; the two store forms are separate instantiations (a run-time branch
+// between two stores of the same values to the same addresses may be folded
+// into the wider one).
 template <int GEN, typename OutT, bool VEC>
-__global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
-                                                     uint64_t *state_out, uint64_t nstreams, uint64_t nper,
-                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out)
+__device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, bool pt, int li, unsigned gmask,
+                                                    OutT *o, uint64_t len, uint32_t *myslot)
 {
-    using P = GmT<GEN>;
-    constexpr int G = P::lanes;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int li = threadIdx.x % G;
-    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1)));
-    if (gid >= nstreams * nsec) return;  // gid is uniform within a group
-    const uint64_t j = gid % nstreams;
-    const uint64_t start = (gid / nstreams) * seclen;
-    if (start >= nper) return;
-    const uint64_t len = min(seclen, nper - start);
-    const bool pt = li < P::s;
-    uint64_t zp = 0, zc = 0;
-    if (pt) {
-        zp = state_in[j * P::s + li] >> P::t;
-        zc = state_in[(nstreams + j) * P::s + li] >> P::t;
-        if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
-    }
-    OutT *o = out + j * nper + start;
+    constexpr int G = GmT<GEN>::lanes;
     const uint64_t full = len / (4 * G);
     for (uint64_t r = 0; r < full; ++r) {
-        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
 #pragma unroll 2
         for (int c = 0; c < G; ++c) {
             const uint32_t a = gm_next_word<GEN>(zc, zp, pt, li, gmask);
             const uint32_t b = gm_next_word<GEN>(zc, zp, pt, li, gmask);
             const uint32_t d = gm_next_word<GEN>(zc, zp, pt, li, gmask);
             const uint32_t e = gm_next_word<GEN>(zc, zp, pt, li, gmask);
-            if (c == li) { w0 = a; w1 = b; w2 = d; w3 = e; }
+            if (c == li) *reinterpret_cast<uint4 *>(myslot) = make_uint4(a, b, d, e);
         }
+        const uint4 wv = *reinterpret_cast<const uint4 *>(myslot);
         OutT *q = o + r * 4 * G + 4 * li;
         if (VEC) {
-            store4<OutT>(q, Cvt<OutT>::f(w0), Cvt<OutT>::f(w1), Cvt<OutT>::f(w2), Cvt<OutT>::f(w3));
+            store4<OutT>(q, Cvt<OutT>::f(wv.x), Cvt<OutT>::f(wv.y), Cvt<OutT>::f(wv.z), Cvt<OutT>::f(wv.w));
         } else {
-            q[0] = Cvt<OutT>::f(w0); q[1] = Cvt<OutT>::f(w1); q[2] = Cvt<OutT>::f(w2); q[3] = Cvt<OutT>::f(w3);
+            q[0] = Cvt<OutT>::f(wv.x); q[1] = Cvt<OutT>::f(wv.y); q[2] = Cvt<OutT>::f(wv.z); q[3] = Cvt<OutT>::f(wv.w);
         }
     }
     const uint32_t rem = (uint32_t)(len - full * 4 * G);  // < 4 G
@@ -349,6 +346,36 @@ __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict_
         if (pos + 2 < rem) q[2] = Cvt<OutT>::f(w2);
         if (pos + 3 < rem) q[3] = Cvt<OutT>::f(w3);
     }
+}
+
+// One group = one section of one stream.  The group of the last section holds
+// the stream's next state and writes it to state_out (a separate buffer when a
+// stream is split into several sections, so no group reads a state another
+// group has already replaced).
+template <int GEN, typename OutT, bool VEC>
+__global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
+                                                     uint64_t *state_out, uint64_t nstreams, uint64_t nper,
+                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out)
+{
+    using P = GmT<GEN>;
+    constexpr int G = P::lanes;
+    __shared__ __align__(16) uint32_t slots[256 * 4];
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int li = threadIdx.x % G;
+    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1)));
+    if (gid >= nstreams * nsec) return;  // gid is uniform within a group
+    const uint64_t j = gid % nstreams;
+    const uint64_t start = (gid / nstreams) * seclen;
+    if (start >= nper) return;
+    const uint64_t len = min(seclen, nper - start);
+    const bool pt = li < P::s;
+    uint64_t zp = 0, zc = 0;
+    if (pt) {
+        zp = state_in[j * P::s + li] >> P::t;
+        zc = state_in[(nstreams + j) * P::s + li] >> P::t;
+        if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
+    }
+    gm_generate_section<GEN, OutT, VEC>(zc, zp, pt, li, gmask, out + j * nper + start, len, slots + 4 * threadIdx.x);
     if (pt && start + len == nper) {
         state_out[j * P::s + li] = gm_canon<GEN>(zp) << P::t;
         state_out[(nstreams + j) * P::s + li] = gm_canon<GEN>(zc) << P::t;

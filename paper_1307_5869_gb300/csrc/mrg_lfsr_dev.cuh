@@ -1,0 +1,116 @@
+// Device routines of MRG32K3A (Sec. 5.2) and LFSR113 (Sec. 5.3) shared by the
+// per-handle kernels and the batched persistent kernel: one recurrence step,
+// and one jump-table application (bit b of an offset).
+#pragma once
+#include "devcommon.cuh"
+
+namespace prand {
+
+// =========================================================== MRG32K3A
+// Matrices of Sec. 5.2 with the negative entries taken mod m.
+__device__ __forceinline__ void mrg_step_matrices(uint32_t A[9], uint32_t B[9])
+{
+    const uint32_t a0[9] = { 0u, 1403580u, kM1 - 810728u, 1u, 0u, 0u, 0u, 1u, 0u };
+    const uint32_t b0[9] = { 527612u, 0u, kM2 - 1370589u, 1u, 0u, 0u, 0u, 1u, 0u };
+    for (int i = 0; i < 9; ++i) { A[i] = a0[i]; B[i] = b0[i]; }
+}
+
+template <uint32_t C>
+__device__ void mat3_sqr(uint32_t M[9])
+{
+    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
+    uint32_t R[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            uint32_t s = 0;
+            for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], M[3 * k + j]), m);
+            R[3 * i + j] = s;
+        }
+    for (int i = 0; i < 9; ++i) M[i] = R[i];
+}
+
+template <uint32_t C>
+__device__ __forceinline__ void mat3_vec(const uint32_t *M, uint32_t v[3])
+{
+    constexpr uint32_t m = (uint32_t)((1ull << 32) - C);
+    uint32_t r[3];
+    for (int i = 0; i < 3; ++i) {
+        uint32_t s = 0;
+        for (int k = 0; k < 3; ++k) s = addmod_u32(s, mulmod_2p32_minus<C>(M[3 * i + k], v[k]), m);
+        r[i] = s;
+    }
+    v[0] = r[0]; v[1] = r[1]; v[2] = r[2];
+}
+
+// Apply the jump of bit b of the table to (x, y).
+__device__ __forceinline__ void mrg_apply_bit(const uint32_t *tab, int b, uint32_t x[3], uint32_t y[3])
+{
+    mat3_vec<209>(tab + 18 * b, x);
+    mat3_vec<22853>(tab + 18 * b + 9, y);
+}
+
+// One step of both components and the output z = (x - y) mod m1 in [1, m1].
+// x_{n+1} = 1403580 x_{n-1} - 810728 x_{n-2} (mod m1)
+// y_{n+1} = 527612 y_n - 1370589 y_{n-2}     (mod m2)
+__device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_t &x2,
+                                             uint32_t &y0, uint32_t &y1, uint32_t &y2)
+{
+    // signed difference of two < 2^53 products, shifted positive by a multiple of m
+    uint64_t u = (uint64_t)1403580u * x1 + (uint64_t)810728u * (uint64_t)kM1 - (uint64_t)810728u * x2;  // < 2^54
+    uint64_t r = (u & 0xFFFFFFFFull) + 209ull * (u >> 32);                                                 // < 2^32 + 2^30
+    uint32_t xn = (uint32_t)(r >= kM1 ? r - kM1 : r);
+    uint64_t w = (uint64_t)527612u * y0 + (uint64_t)1370589u * (uint64_t)kM2 - (uint64_t)1370589u * y2;   // < 2^54
+    uint64_t s = (w & 0xFFFFFFFFull) + 22853ull * (w >> 32);                                               // < 2^32 + 2^37
+    s = (s & 0xFFFFFFFFull) + 22853ull * (s >> 32);                                                        // < 2^32 + 2^20
+    uint32_t yn = (uint32_t)(s >= kM2 ? s - kM2 : s);
+    x2 = x1; x1 = x0; x0 = xn;
+    y2 = y1; y1 = y0; y0 = yn;
+    return xn > yn ? xn - yn : xn - yn + kM1;
+}
+
+
+// =========================================================== LFSR113
+// Component (p, q, s): (31,6,18), (29,2,2), (28,13,7), (25,3,13).  The word
+// holds bits x_{ns}..x_{ns+31} of eq. (lfsrOutput); a step keeps the top p bits
+// shifted by s and refills the rest through eq. (lfsrRel1).
+template <int P, int Q, int S>
+__host__ __device__ __forceinline__ uint32_t taus_step(uint32_t z)
+{
+    constexpr uint32_t mask = 0xFFFFFFFFu << (32 - P);
+    return ((z & mask) << S) ^ (((z << Q) ^ z) >> (P - S));
+}
+
+__device__ __forceinline__ uint32_t lfsr_comp_step(int c, uint32_t z)
+{
+    switch (c) {
+    case 0: return taus_step<31, 6, 18>(z);
+    case 1: return taus_step<29, 2, 2>(z);
+    case 2: return taus_step<28, 13, 7>(z);
+    default: return taus_step<25, 3, 13>(z);
+    }
+}
+
+__device__ __forceinline__ uint32_t gf2_apply(const uint32_t *col, uint32_t v)
+{
+    uint32_t r = 0;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) r ^= ((v >> i) & 1u) ? col[i] : 0u;
+    return r;
+}
+
+__device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint32_t z[4])
+{
+    for (int c = 0; c < 4; ++c) z[c] = gf2_apply(tab + ((size_t)c * kJumpBits + b) * 32, z[c]);
+}
+
+__device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)
+{
+    z0 = taus_step<31, 6, 18>(z0);
+    z1 = taus_step<29, 2, 2>(z1);
+    z2 = taus_step<28, 13, 7>(z2);
+    z3 = taus_step<25, 3, 13>(z3);
+    return z0 ^ z1 ^ z2 ^ z3;
+}
+
+
+}  // namespace prand
