@@ -97,21 +97,42 @@ __device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t zc, uint64_t zp
     uint64_t h = S >> 51;                                  // < 2^10
     return S - h * p;                                      // (S mod 2^51) + 129 h < 2^51 + 2^18
 }
-// p = 2^61 - 1; lazy z < 2^61 + 256.  32-bit limbs: with t = 2p - y,
-// A = 24 z0 + 74 t0 and B = 24 z1 + 74 t1 + A.hi (four 32x32->64 multiply-adds)
-// give S = 24 z + 74 t = A.lo + 2^32 B < 2^69.  With h = S >> 61 = B >> 29 and
-// m = B mod 2^29 = b0 - h 2^29, the fold is R = A.lo + h + 2^32 m.
-template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GM61>(uint64_t zc, uint64_t zp)
+// p = 2^61 - 1.  Generation runs on u = (2 z mod p) + 1 rather than on z.
+// Doubling modulo a Mersenne prime rotates the 61-bit residue left by one bit,
+// so bit 60 of z -- the output bit floor(2 z / p) -- lands on bit 0; since the
+// map is linear the doubled values obey the same recurrence, and the offset
+// turns it into u' = 24 u - 74 u_prev + 51 (mod p).  Residues stay lazy in
+// [1, 2^61 + 256): a value u >= 2^61 stands for u - p, whose bit 0 is the
+// complement of u's, so the output bit is XNOR(bit 0 of u, bit 61 of u) --
+// one logic operation instead of a 64-bit range test.
+__device__ __forceinline__ uint64_t gm61_enter(uint64_t z)  // z lazy (< 2^61 + 256) -> u
 {
-    const uint32_t z0 = (uint32_t)zc, z1 = (uint32_t)(zc >> 32);
-    const uint32_t y0 = (uint32_t)zp, y1 = (uint32_t)(zp >> 32);
+    constexpr uint64_t p = (1ull << 61) - 1;
+    const uint64_t c = z >= p ? z - p : z;
+    return (((c << 1) & p) | (c >> 60)) + 1;
+}
+__device__ __forceinline__ uint64_t gm61_leave(uint64_t u)  // u -> canonical z
+{
+    constexpr uint64_t p = (1ull << 61) - 1;
+    uint64_t w = u - 1;
+    if (w >= p) w -= p;
+    return (w >> 1) | ((w & 1) << 60);
+}
+// One step on (u, u_prev) in 32-bit limbs.  With t = C - u_prev, where
+// C = 0x23E45306EB3E4530 > 2^61 + 2^12 and 74 C = 51 (mod p),
+// S = 24 u + 74 t = u' (mod p); A = 74 t0 + 24 u0, B = 74 t1 + 24 u1 + A.hi
+// (< 2^37), h = B >> 29 and S = A.lo + h + 2^32 (B mod 2^29) (mod p), which is
+// >= 1 because S > 0.  Returns the output bit of the new value.
+__device__ __forceinline__ bool gm61_step(uint64_t &uc, uint64_t &up)
+{
+    const uint32_t u0 = (uint32_t)uc, u1 = (uint32_t)(uc >> 32);
+    const uint32_t v0 = (uint32_t)up, v1 = (uint32_t)(up >> 32);
     uint32_t r0, r1;
     asm("{\n\t"
         ".reg .u32 t0, t1, a0, a1, b0, b1, h, m;\n\t"
         ".reg .u64 A, B, T;\n\t"
-        "sub.cc.u32 t0, 0xFFFFFFFE, %2;\n\t"
-        "subc.u32 t1, 0x3FFFFFFF, %3;\n\t"
+        "sub.cc.u32 t0, 0xEB3E4530, %2;\n\t"
+        "subc.u32 t1, 0x23E45306, %3;\n\t"
         "mul.wide.u32 T, t0, 74;\n\t"
         "mad.wide.u32 A, %4, 24, T;\n\t"
         "mov.b64 {a0, a1}, A;\n\t"
@@ -125,8 +146,10 @@ __device__ __forceinline__ uint64_t gm_step<PRAND_GM61>(uint64_t zc, uint64_t zp
         "addc.u32 %1, m, 0;\n\t"
         "}"
         : "=r"(r0), "=r"(r1)
-        : "r"(y0), "r"(y1), "r"(z0), "r"(z1));
-    return ((uint64_t)r1 << 32) | r0;
+        : "r"(v0), "r"(v1), "r"(u0), "r"(u1));
+    up = uc;
+    uc = ((uint64_t)r1 << 32) | r0;
+    return (((r0 << 29) ^ ~r1) & 0x20000000u) != 0;
 }
 // p = 2^29 - 3 (GQ58.x, z = x / 2^29); lazy z < 2^29 + 384
 template <>
@@ -147,13 +170,9 @@ __device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_4>(uint64_t zc, uint64_t 
 // floor(2^v z / p) of the canonical residue = floor(2^v x / g): the strip of the
 // torus the point lies in, evaluated on the lazy value z.
 template <int GEN>
-__device__ __forceinline__ bool gm_strip1(uint64_t z)  // v = 1: canonical z in [(p+1)/2, p)
+__device__ __forceinline__ bool gm_strip1(uint64_t z)  // v = 1, p < 2^32: canonical z in [(p+1)/2, p)
 {
     using P = GmT<GEN>;
-    if (P::kind == P61) {
-        // z < 2^61 + 256: canonical z >= 2^60  <=>  2^60 <= z < p
-        return z - (1ull << 60) <= (1ull << 60) - 2;
-    }
     constexpr uint32_t half = (uint32_t)((P::p + 1) / 2);
     return (uint32_t)z - half < (uint32_t)(P::p - half);
 }
@@ -287,12 +306,17 @@ template <int GEN>
 __device__ __forceinline__ uint32_t gm_next_word(uint64_t &zc, uint64_t &zp, bool pt, int li, unsigned gmask)
 {
     using P = GmT<GEN>;
-    const uint64_t zn = gm_step<GEN>(zc, zp);
-    zp = zc;
-    zc = zn;
-    if (P::v == 1) return __ballot_sync(gmask, pt && gm_strip1<GEN>(zn));
-    const uint32_t w = (pt && P::v * li < 32) ? (gm_strip<GEN>(zn) << (P::v * li)) : 0u;
-    return __reduce_or_sync(gmask, w);
+    if constexpr (GEN == PRAND_GM61) {  // (zc, zp) hold the rotated values u
+        const bool b = gm61_step(zc, zp);
+        return __ballot_sync(gmask, pt && b);
+    } else {
+        const uint64_t zn = gm_step<GEN>(zc, zp);
+        zp = zc;
+        zc = zn;
+        if (P::v == 1) return __ballot_sync(gmask, pt && gm_strip1<GEN>(zn));
+        const uint32_t w = (pt && P::v * li < 32) ? (gm_strip<GEN>(zn) << (P::v * li)) : 0u;
+        return __reduce_or_sync(gmask, w);
+    }
 }
 
 // One group generates `len` outputs of one section into o: rounds of 4 * lanes
@@ -311,9 +335,10 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, 
                                                     OutT *o, uint64_t len, uint32_t *myslot)
 {
     constexpr int G = GmT<GEN>::lanes;
+    if constexpr (GEN == PRAND_GM61) { zc = gm61_enter(zc); zp = gm61_enter(zp); }
     const uint64_t full = len / (4 * G);
     for (uint64_t r = 0; r < full; ++r) {
-#pragma unroll 2
+#pragma unroll (GEN == PRAND_GM61 ? 4 : 2)
         for (int c = 0; c < G; ++c) {
             const uint32_t a = gm_next_word<GEN>(zc, zp, pt, li, gmask);
             const uint32_t b = gm_next_word<GEN>(zc, zp, pt, li, gmask);
@@ -346,6 +371,7 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, 
         if (pos + 2 < rem) q[2] = Cvt<OutT>::f(w2);
         if (pos + 3 < rem) q[3] = Cvt<OutT>::f(w3);
     }
+    if constexpr (GEN == PRAND_GM61) { zc = gm61_leave(zc); zp = gm61_leave(zp); }
 }
 
 // One group = one section of one stream.  The group of the last section holds
