@@ -30,15 +30,24 @@ from paper_1307_5869_gb300 import workloads as W  # noqa: E402
 METRIC = "GSamples/s (uint32) per generator, 2^30 outputs; % of HBM-write/int-pipe roofline"
 UNIT = "GSamples/s"
 WORKLOAD = ("bulk fill: MT19937, LFSR113, GM61; 2^20 block-split streams x (2^10 u32 + 2^10 f32) "
-            "outputs per generator per step; seed = 0x9E3779B97F4A7C15 + rank")
+            "outputs per generator per GPU per step; seed 0x9E3779B97F4A7C15; rank r takes streams "
+            "[r 2^20, (r+1) 2^20)")
 
 # Algorithmic work per output (measurement section).
 STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 16, "GM29": 32 * 16,
                "GM31": 32 * 16, "GM55": 8 * 16, "GM61": 32 * 16, "GQ58_1": 32 * 16, "GQ58_3": 12 * 16,
                "GQ58_4": 8 * 16}
-# int32 operations per torus point step for the 61-bit Mersenne modulus, times 32 points per word
-GM61_OPS_PER_WORD = 24 * 32
+# int32 operations per torus point step of GM61 (x' = 24 x - 74 x_prev mod 2^61 - 1) on
+# 32-bit lanes: the two-limb negation of x_prev (2), four 32x32->64 multiply-adds counted as
+# two operations each (8), the Mersenne fold (high bits, low mask, two-limb add: 4), the
+# output bit (1) and the warp ballot that assembles the word (1) -- 16 per point, 32 points
+# per output word
+GM61_OPS_PER_WORD = 16 * 32
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
+# output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
+# third of a second of demand).
+SERVE_OUTPUT_BYTES = 32 << 30
 
 
 def _peaks():
@@ -191,8 +200,8 @@ def run_gpu(args):
     for g in gens:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = P.prand_create(g, W.bulk_seed(rank))
-        P.prand_init_streams(h, rank * nS, nS)
+        h = P.prand_create(g, W.bulk_seed(0))
+        P.prand_init_streams(h, *W.shard_range(rank, world, nS))
         init_ms[g] = 1e3 * (time.perf_counter() - t0)
         handles[g] = h
     U = torch.empty(nS * nP, dtype=torch.int32, device="cuda")
@@ -300,6 +309,10 @@ def run_gpu(args):
     del U, F
     torch.cuda.empty_cache()
 
+    table = single = None
+    if not args.no_table and rank == 0:
+        table = run_table(P, torch, sp, args)
+        single = run_single(P, torch, sp, args)
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(P, torch, sp, args)
@@ -324,6 +337,8 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": e2e,
+            "table": table,
+            "single_stream": single,
             "batched": batched,
             "serving": serving,
         }
@@ -342,6 +357,70 @@ def run_gpu(args):
     if line is not None:
         print(json.dumps(line))
     return 0
+
+
+def _time_calls(torch, stream, fn, warmup=3, reps=5):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_table(P, torch, sp, args):
+    """All eleven generators, 2^16 block-split streams x 2^12 outputs (u32, then
+    f32 on the continued streams), seed 12345: device time per fill (CUDA
+    events, 5 timed fills after 3 warm-up fills; 1 GiB per fill >> L2).  HBM
+    bytes = outputs + state read and written; the GM/GQ fills are integer-pipe
+    bound, so their HBM fraction is small by nature."""
+    hbm_peak, _ = _peaks()
+    stream = torch.cuda.current_stream()
+    nS, nP = W.TABLE_STREAMS, W.TABLE_PER_STREAM
+    U = torch.empty(nS * nP, dtype=torch.int32, device="cuda")
+    out = {}
+    for g in W.GENERATORS:
+        h = P.prand_create(g, W.TABLE_SEED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.prand_init_streams(h, 0, nS)
+        torch.cuda.synchronize()
+        init_ms = 1e3 * (time.perf_counter() - t0)
+        res = {"init_ms": init_ms}
+        for dt, fn in (("u32", P.prand_generate_u32), ("f32", P.prand_generate_f32)):
+            ms = _time_calls(torch, stream, lambda: fn(h, U.data_ptr(), nP, sp))
+            byts = nS * nP * 4 + 2 * nS * STATE_BYTES[g]
+            res[dt] = {"ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9,
+                       "hbm_frac": byts / (ms * 1e-3) / 1e9 / hbm_peak}
+        P.prand_destroy(h)
+        out[g] = res
+    del U
+    torch.cuda.empty_cache()
+    return {"workload": "11 generators x 2^16 streams x 2^12 outputs (u32, then f32), seed 12345",
+            "generators": out}
+
+
+def run_single(P, torch, sp, args):
+    """One MRG32K3A stream from the default state, 2^20 outputs (u32 and f64):
+    the launch- and latency-bound case (the library splits the stream into
+    sections).  Device time per call, CUDA events over 50 calls (the 4-8 MiB
+    output stays in L2)."""
+    stream = torch.cuda.current_stream()
+    n = W.SINGLE_LENGTH
+    buf = torch.empty(n, dtype=torch.float64, device="cuda")
+    h = P.prand_create("MRG32K3A", P.SEED_DEFAULT)
+    P.prand_init_streams(h, 0, 1)
+    res = {}
+    for dt, fn in (("u32", P.prand_generate_u32), ("f64", P.prand_generate_f64)):
+        ms = _time_calls(torch, stream, lambda: fn(h, buf.data_ptr(), n, sp), warmup=5, reps=50)
+        res[dt] = {"us": 1e3 * ms, "gsamples_per_s": n / (ms * 1e-3) / 1e9}
+    P.prand_destroy(h)
+    del buf
+    return {"workload": "MRG32K3A, default state, 1 stream x 2^20 outputs", **res}
 
 
 def run_batched(P, torch, sp, args):
@@ -404,7 +483,7 @@ def run_serving(P, args):
     arr = W.serving_arrivals(rate=args.serve_rate, seconds=args.serve_seconds, seed=11)
     reqs = [(g, d, k, n) for _, g, k, n, d in arr]
     times = [t for t, _, _, _, _ in arr]
-    srv = P.prand_server_create(11, 8 << 30, 65536)
+    srv = P.prand_server_create(11, SERVE_OUTPUT_BYTES, 65536)
     try:
         lat, wall = P.prand_server_replay(srv, reqs, times)
         st = P.prand_server_stats(srv)
@@ -434,6 +513,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-per-request", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=5e4)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

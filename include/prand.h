@@ -145,6 +145,22 @@ const char *prand_status_string(prand_status_t status);
 /* Number of device kernels this library has launched in the process. */
 uint64_t prand_kernel_launches(void);
 
+/* The float maps on their own (Sec. 7.3 asks only for outputs uniform in
+ * [0, 1); the exact maps are this library's reading, the same ones every
+ * prand_generate_f32 / _f64 call applies):
+ *   map = PRAND_DTYPE_F32:   out[i] = (float)(in[i] >> 8) * 2^-24     in [0, 1)
+ *   map = PRAND_DTYPE_F64:   out[i] = (double)in[i] * 2^-32           in [0, 1), exact
+ *   map = PRAND_MAP_MRG_F64: out[i] = (double)in[i] * RN(1 / (m1 + 1)), one
+ *                            round-to-nearest multiply (MRG32K3A's map; in (0, 1)
+ *                            for its outputs z in [1, m1])
+ * dev_in: n caller-owned 32-bit words in device memory (4-byte aligned);
+ * dev_out: n floats or doubles, caller-owned, aligned to the element size (may
+ * not overlap dev_in).  Asynchronous on `stream`.
+ * Errors: PRAND_ERR_ARG (null pointer with n > 0, unknown map), PRAND_ERR_ALIGN,
+ * PRAND_ERR_CUDA (launch failure). */
+#define PRAND_MAP_MRG_F64 3
+prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out, cudaStream_t stream);
+
 /* One batched request: `length` outputs of stream `stream` of generator `gen`
  * (seeded with the batch's seed), starting at the stream's beginning, written
  * to dev_out (caller-owned, aligned to the element size of `dtype`). */

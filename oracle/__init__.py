@@ -68,6 +68,7 @@ def lib():
             L.orc_u32_to_f64.restype = ctypes.c_double
             L.orc_mrg_to_f64.argtypes = [ctypes.c_uint32]
             L.orc_mrg_to_f64.restype = ctypes.c_double
+            L.orc_convert.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp]
             L.orc_mt_charpoly.argtypes = [u64p]
             L.orc_mt_jump_poly.argtypes = [u64p, u64p]
             L.orc_mt_x_pow2k.argtypes = [ctypes.c_int, u64p]
@@ -84,6 +85,16 @@ def lib():
             L.orc_gm_point_jump.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p, u64p]
             _lib = L
     return _lib
+
+
+def convert(u: np.ndarray, kind: str) -> np.ndarray:
+    """The float maps applied to an array of u32 words: kind "f32", "f64" or
+    "mrg_f64" (the MRG32K3A double map)."""
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    k = {"f32": 0, "f64": 1, "mrg_f64": 2}[kind]
+    out = np.empty(u.size, dtype=np.float32 if k == 0 else np.float64)
+    lib().orc_convert(u.ctypes.data, u.size, k, out.ctypes.data)
+    return out
 
 
 def big(n: int, words: int = NBIG):

@@ -94,6 +94,17 @@ double orc_u32_to_f64(uint32_t u) { return (double)u * 0x1p-32; }
 static const double MRG_NORM = 1.0 / 4294967088.0;
 double orc_mrg_to_f64(uint32_t z) { return (double)z * MRG_NORM; }
 
+/* The three float maps over an array (kind 0: f32, 1: f64, 2: MRG32K3A f64),
+ * one value at a time with the functions above. */
+void orc_convert(const uint32_t *in, uint64_t n, int kind, void *out)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        if (kind == 0) ((float *)out)[i] = orc_u32_to_f32(in[i]);
+        else if (kind == 1) ((double *)out)[i] = orc_u32_to_f64(in[i]);
+        else ((double *)out)[i] = orc_mrg_to_f64(in[i]);
+    }
+}
+
 /* ================================================================== */
 /* MT19937 (Matsumoto & Nishimura 1998; Sec. 5.4)                      */
 /* ================================================================== */

@@ -37,7 +37,7 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_batch_plan_launch", "prand_batch_plan_destroy", "prand_batch_autotune",
            "prand_mrg32k3a_generate_u32_noalloc", "prand_server_create", "prand_server_submit",
            "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
-           "prand_server_destroy", "prand_server_replay"]
+           "prand_server_destroy", "prand_server_replay", "prand_convert"]
 
 
 class PrandError(RuntimeError):
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
     L.prand_kernel_launches.restype = u64
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
     L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
+    L.prand_convert.argtypes = [ctypes.c_void_p, u64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     vp = ctypes.c_void_p
     L.prand_server_create.argtypes = [ctypes.POINTER(vp), u64, u64, ctypes.c_uint32]
     L.prand_server_submit.argtypes = [vp, ctypes.c_int32, u64, u64, ctypes.c_int32, ctypes.POINTER(u64)]
@@ -243,6 +244,14 @@ def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out:
     """MRG32K3A u32 fill on caller-held states without any device allocation."""
     _check(load().prand_mrg32k3a_generate_u32_noalloc(dev_state, n_streams, dev_out, n_per_stream, stream),
            "prand_mrg32k3a_generate_u32_noalloc")
+
+
+MAP_MRG_F64 = 3
+
+
+def prand_convert(dev_in: int, n: int, map_: int, dev_out: int, stream: int = 0) -> None:
+    """Float map of n device u32 words: map_ = DTYPE_F32, DTYPE_F64 or MAP_MRG_F64."""
+    _check(load().prand_convert(dev_in, n, map_, dev_out, stream), "prand_convert")
 
 
 def prand_server_create(seed: int, output_bytes: int, slots_per_generator: int) -> int:

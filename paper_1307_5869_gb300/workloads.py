@@ -23,6 +23,16 @@ def bulk_seed(rep: int = 0) -> int:
     return (BULK_SEED_BASE + rep) & 0xFFFFFFFFFFFFFFFF
 
 
+def shard_range(rank: int, world: int, per_rank: int, first: int = 0):
+    """Streams of one rank when a job is sharded by stream index: every rank
+    uses the same seed and takes the contiguous range [first + rank * per_rank,
+    first + (rank + 1) * per_rank), so the ranks' outputs together are the
+    outputs of one job over world * per_rank streams (weak scaling)."""
+    if not 0 <= rank < world or per_rank < 0:
+        raise ValueError("rank must be in [0, world) and per_rank >= 0")
+    return first + rank * per_rank, per_rank
+
+
 # All eleven generators, 2^16 streams x 2^12 outputs, seed 12345.
 TABLE_STREAMS = 1 << 16
 TABLE_PER_STREAM = 1 << 12

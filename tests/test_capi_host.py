@@ -62,6 +62,12 @@ def test_argument_errors_without_device(lib):
     bad = (P.Request * 1)(P.Request(0, 7, 0, 1, 0))
     assert L.prand_batch_run(bad, 1, 0, None) == 1
     assert L.prand_batch_run(None, 0, 0, None) == 0              # empty batch
+    vp = ctypes.c_void_p
+    assert L.prand_convert(None, 1, 1, vp(0x1000), None) == 1    # NULL input
+    assert L.prand_convert(vp(0x1000), 1, 7, vp(0x2000), None) == 1  # unknown map
+    assert L.prand_convert(None, 0, 1, None, None) == 0           # nothing to do
+    assert L.prand_convert(vp(0x1002), 4, 1, vp(0x2000), None) == 2  # input not 4-byte aligned
+    assert L.prand_convert(vp(0x1000), 4, 2, vp(0x2004), None) == 2  # doubles not 8-byte aligned
 
 
 def test_binding_raises_on_error(lib):
