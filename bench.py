@@ -44,6 +44,12 @@ STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 1
 # per output word
 GM61_OPS_PER_WORD = 16 * 32
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) per stream of one fill of 1024 outputs, from one ncu
+# capture of the current kernels at that shape (profiles/traffic_bulk_fill.md);
+# None for other shapes.
+TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.3217e9 / 2**18, "MT19937.f32": 2.3207e9 / 2**18,
+                           "LFSR113.u32": 1.0222e9 / 2**18, "LFSR113.f32": 1.0224e9 / 2**18,
+                           "GM61.u32": 1.2781e9 / 2**18, "GM61.f32": 1.2788e9 / 2**18}
 # Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
@@ -264,6 +270,8 @@ def run_gpu(args):
                                   "unit": "GB/s", "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9,
                                   "traffic": None}
             rooflines[key]["frac"] = rooflines[key]["achieved"] / rooflines[key]["peak"]
+            tr = TRAFFIC_PER_STREAM_1024.get(key) if nP == 1024 else None
+            rooflines[key]["traffic"] = tr * nS if tr else None
     # dominant kernel = the launch with the largest share of the step
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
     R = rooflines[dom]
