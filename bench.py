@@ -287,16 +287,21 @@ def run_gpu(args):
         hu = torch.empty(nS * nP, dtype=torch.int32, pin_memory=True)
         hf = torch.empty(nS * nP, dtype=torch.float32, pin_memory=True)
 
+        call_ms = {}
+
         def e2e_step():
+            # the library's host-array fill: generation in blocks on the device,
+            # each block's copy into the page-locked arrays overlapping the next
             for g in gens:
-                P.prand_generate_u32(handles[g], U.data_ptr(), nP, sp)
-                hu.copy_(U, non_blocking=True)
-                P.prand_generate_f32(handles[g], F.data_ptr(), nP, sp)
-                hf.copy_(F, non_blocking=True)
-            torch.cuda.synchronize()
+                for dt, fn, buf in (("u32", P.prand_generate_host_u32, hu), ("f32", P.prand_generate_host_f32, hf)):
+                    t = time.perf_counter()
+                    fn(handles[g], buf.data_ptr(), nP, sp)
+                    call_ms.setdefault(f"{g}.{dt}", []).append(1e3 * (time.perf_counter() - t))
             return int(hu[0]) + int(hf[0] > 2)  # read back a result on the host
 
-        e2e_step()
+        for _ in range(2):  # warm-up: staging allocation, first touch of the host arrays
+            e2e_step()
+        call_ms.clear()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
@@ -309,7 +314,8 @@ def run_gpu(args):
             dt = float(t.item())
         e2e = {"value": world * samples_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(gens) * nS * nP * 8,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps, "api": "prand_generate_host_u32 / _f32 into page-locked host arrays",
+               "call_ms": {k: statistics.median(v) for k, v in call_ms.items()}}
         del hu, hf
 
     for h in handles.values():
@@ -515,7 +521,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -116,6 +116,24 @@ prand_status_t prand_generate_u32(prand_handle_t h, uint32_t *dev_out, uint64_t 
 prand_status_t prand_generate_f32(prand_handle_t h, float *dev_out, uint64_t n_per_stream, prand_stream_t stream);
 prand_status_t prand_generate_f64(prand_handle_t h, double *dev_out, uint64_t n_per_stream, prand_stream_t stream);
 
+/* The same fills into HOST memory (the paper's host-array fill,
+ * rng_generate_array_, Sec. 7.5): host_out[j * n_per_stream + i] = output i of
+ * stream j, the values prand_generate_* would write.  host_out is
+ * caller-owned host memory aligned to the element size; page-locked memory
+ * (cudaMallocHost / cudaHostRegister) gives full copy bandwidth, pageable
+ * memory works but copies more slowly.  The outputs are generated on the
+ * device in blocks that fit a staging area owned by the handle (two buffers of
+ * 256 MiB, or PRAND_HOST_STAGE_BYTES from the environment at the handle's first
+ * host fill, allocated then and freed by prand_destroy), each block's copy
+ * overlapping the next block's generation.  Generation runs on `stream`
+ * (after work already queued there); the call returns once every output is in
+ * host_out.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_STATE, PRAND_ERR_NOMEM
+ * (staging), PRAND_ERR_CUDA. */
+prand_status_t prand_generate_host_u32(prand_handle_t h, uint32_t *host_out, uint64_t n_per_stream, prand_stream_t stream);
+prand_status_t prand_generate_host_f32(prand_handle_t h, float *host_out, uint64_t n_per_stream, prand_stream_t stream);
+prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint64_t n_per_stream, prand_stream_t stream);
+
 /* Advance every stream of the handle by the 256-bit offset offset_le[0] +
  * 2^64 offset_le[1] + 2^128 offset_le[2] + 2^192 offset_le[3] outputs
  * (rng_skipahead_, Sec. 7.2; jump methods of Sec. 5.1-5.4).

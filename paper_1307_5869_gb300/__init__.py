@@ -37,7 +37,8 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_batch_plan_launch", "prand_batch_plan_destroy", "prand_batch_autotune",
            "prand_mrg32k3a_generate_u32_noalloc", "prand_server_create", "prand_server_submit",
            "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
-           "prand_server_destroy", "prand_server_replay", "prand_convert"]
+           "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
+           "prand_generate_host_f32", "prand_generate_host_f64"]
 
 
 class PrandError(RuntimeError):
@@ -74,7 +75,8 @@ def load(build_if_missing: bool = False):
     u64 = ctypes.c_uint64
     L.prand_create.argtypes = [ctypes.POINTER(H), ctypes.c_int, u64]
     L.prand_init_streams.argtypes = [H, u64, u64]
-    for nm in ("prand_generate_u32", "prand_generate_f32", "prand_generate_f64"):
+    for nm in ("prand_generate_u32", "prand_generate_f32", "prand_generate_f64", "prand_generate_host_u32",
+               "prand_generate_host_f32", "prand_generate_host_f64"):
         getattr(L, nm).argtypes = [H, ctypes.c_void_p, u64, ctypes.c_void_p]
     L.prand_skipahead.argtypes = [H, ctypes.POINTER(u64)]
     L.prand_get_state.argtypes = [H, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
@@ -153,6 +155,18 @@ def prand_generate_f32(h: int, dev_out: int, n_per_stream: int, stream: int = 0)
 
 def prand_generate_f64(h: int, dev_out: int, n_per_stream: int, stream: int = 0) -> None:
     _check(load().prand_generate_f64(h, dev_out, n_per_stream, stream), "prand_generate_f64")
+
+
+def prand_generate_host_u32(h: int, host_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_host_u32(h, host_out, n_per_stream, stream), "prand_generate_host_u32")
+
+
+def prand_generate_host_f32(h: int, host_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_host_f32(h, host_out, n_per_stream, stream), "prand_generate_host_f32")
+
+
+def prand_generate_host_f64(h: int, host_out: int, n_per_stream: int, stream: int = 0) -> None:
+    _check(load().prand_generate_host_f64(h, host_out, n_per_stream, stream), "prand_generate_host_f64")
 
 
 def prand_skipahead(h: int, offset: int) -> None:

@@ -29,20 +29,6 @@
 
 namespace prand {
 
-prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                             cudaStream_t st);
-prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
-                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped);
-prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                       cudaStream_t st);
-prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out, int dtype,
-                      uint64_t nper, cudaStream_t st, bool *swapped);
-prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
-prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
-
 constexpr int kBatchThreads = 64;  // small blocks: a warp on a long tile (an MT19937 jump chain) holds little besides itself
 constexpr int kWarpSmem = 5120;  // max of: MT 2 x 624 words, staged row tile 32 x 144 B, GM word slots
 
@@ -704,17 +690,18 @@ prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n
         const prand_request_t &r = reqs[i];
         if (!r.length) continue;
         void *a = (char *)scratch + 2 * maxb * i, *b = (char *)a + maxb;
-        bool sw = false;
+        StreamRange R;
+        R.stride = R.count = 1;
         uint32_t idx = kMtN;
         if (r.gen == PRAND_MT19937) {
             s = mt_init(T, ctx.base[r.gen], a, r.stream, 1, st);
             if (s == PRAND_OK) s = mt_gen(a, 1, &idx, r.dev_out, r.dtype, r.length, st);
         } else if (is_gm(r.gen)) {
             s = gm_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
-            if (s == PRAND_OK) s = gm_gen(r.gen, T, a, b, 1, r.dev_out, r.dtype, r.length, st, &sw);
+            if (s == PRAND_OK) s = gm_gen(r.gen, T, a, b, R, r.dev_out, r.dtype, r.length, st);
         } else {
             s = mrg_lfsr_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
-            if (s == PRAND_OK) s = mrg_lfsr_gen(r.gen, T, a, b, 1, r.dev_out, r.dtype, r.length, st, &sw);
+            if (s == PRAND_OK) s = mrg_lfsr_gen(r.gen, T, a, b, R, r.dev_out, r.dtype, r.length, st);
         }
     }
     // scratch is freed in stream order (the runtime defers it until the work is done)

@@ -3,33 +3,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 
 #include "prand_internal.h"
 
 namespace prand {
-
-// family entry points (gen_*.cu)
-prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st);
-prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st);
-prand_status_t gm_build_table(int gen, uint64_t *tab, cudaStream_t st);
-prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                             cudaStream_t st);
-prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
-prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
-                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped);
-prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                       cudaStream_t st);
-prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
-prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out, int dtype,
-                      uint64_t nper, cudaStream_t st, bool *swapped);
-prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
-prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st);
-prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
 
 std::atomic<uint64_t> g_launches{ 0 };
 
@@ -111,6 +91,11 @@ struct prand_handle_s {
     uint64_t position = 0;
     uint32_t mt_idx = kMtN;
     cudaStream_t last_stream = 0;
+    // host fills: two device staging buffers, a copy stream and its events
+    void *stage[2] = {};
+    uint64_t stage_bytes = 0;
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_gen[2] = {}, ev_copy[2] = {};
 };
 
 namespace {
@@ -162,15 +147,132 @@ prand_status_t generate_any(prand_handle_t h, void *out, int dtype, uint64_t npe
     if (mul_overflows(h->n, nper, &total) || mul_overflows(total, esz, &bytes)) return PRAND_ERR_ARG;
     if (nper == 0) return PRAND_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    bool swapped = false;
+    StreamRange R;
+    R.stride = R.count = h->n;
     if (h->gen == PRAND_MT19937) s = mt_gen(h->d_state, h->n, &h->mt_idx, out, dtype, nper, st);
-    else if (is_gm(h->gen)) s = gm_gen(h->gen, h->T, h->d_state, h->d_spare, h->n, out, dtype, nper, st, &swapped);
-    else s = mrg_lfsr_gen(h->gen, h->T, h->d_state, h->d_spare, h->n, out, dtype, nper, st, &swapped);
+    else if (is_gm(h->gen)) s = gm_gen(h->gen, h->T, h->d_state, h->d_spare, R, out, dtype, nper, st);
+    else s = mrg_lfsr_gen(h->gen, h->T, h->d_state, h->d_spare, R, out, dtype, nper, st);
     if (s != PRAND_OK) return s;
-    if (swapped) { void *t = h->d_state; h->d_state = h->d_spare; h->d_spare = t; }
+    if (R.nsec > 1) { void *t = h->d_state; h->d_state = h->d_spare; h->d_spare = t; }
     h->position += nper;
     h->last_stream = st;
     return PRAND_OK;
+}
+
+// Staging for host fills, allocated on first use: 256 MiB per buffer unless
+// PRAND_HOST_STAGE_BYTES asks for another size (at least 4 KiB).
+constexpr uint64_t kStageBytesDefault = 256ull << 20;
+
+void free_staging(prand_handle_t h)
+{
+    for (int b = 0; b < 2; ++b) {
+        if (h->stage[b]) cudaFree(h->stage[b]);
+        if (h->ev_gen[b]) cudaEventDestroy(h->ev_gen[b]);
+        if (h->ev_copy[b]) cudaEventDestroy(h->ev_copy[b]);
+        h->stage[b] = nullptr;
+        h->ev_gen[b] = h->ev_copy[b] = nullptr;
+    }
+    if (h->copy_st) cudaStreamDestroy(h->copy_st);
+    h->copy_st = nullptr;
+    h->stage_bytes = 0;
+}
+
+prand_status_t ensure_staging(prand_handle_t h)
+{
+    if (h->stage[0]) return PRAND_OK;
+    uint64_t bytes = kStageBytesDefault;
+    if (const char *e = getenv("PRAND_HOST_STAGE_BYTES")) {
+        const unsigned long long v = strtoull(e, nullptr, 10);
+        if (v >= 4096) bytes = (uint64_t)v & ~255ull;
+    }
+    h->stage_bytes = bytes;
+    bool ok = cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaMalloc(&h->stage[b], bytes) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_gen[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_copy[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        free_staging(h);
+        return PRAND_ERR_NOMEM;
+    }
+    return PRAND_OK;
+}
+
+// The host-array fill: the outputs are generated on the device in blocks of
+// (streams x outputs) that fit a staging buffer and copied into host_out, the
+// copy of one block overlapping the generation of the next (two buffers, two
+// streams).  Output blocks run in order; within one, the stream blocks share
+// one section split, so their next states land in the same buffer.
+prand_status_t generate_host(prand_handle_t h, void *host_out, int dtype, uint64_t nper, prand_stream_t stream)
+{
+    if (!h || !host_out) return PRAND_ERR_ARG;
+    const size_t esz = dtype == PRAND_DTYPE_F64 ? 8 : 4;
+    if ((uintptr_t)host_out % esz) return PRAND_ERR_ALIGN;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    uint64_t total, bytes;
+    if (mul_overflows(h->n, nper, &total) || mul_overflows(total, esz, &bytes)) return PRAND_ERR_ARG;
+    if (nper == 0) return PRAND_OK;
+    if ((s = ensure_staging(h)) != PRAND_OK) return s;
+    const uint64_t n = h->n, stage = h->stage_bytes;
+    // outputs per block: whole rows when 65536 streams (or all) fit, else
+    // shorter rows (multiples of 64 outputs)
+    const uint64_t rows = std::min<uint64_t>(n, 65536);
+    uint64_t k = nper;
+    if (k > stage / (esz * rows)) k = std::max<uint64_t>(64, (stage / (esz * rows)) & ~63ull);
+    if (k > nper) k = nper;
+    const uint64_t cs = std::max<uint64_t>(1, std::min<uint64_t>(n, stage / (k * esz)));
+    cudaStream_t st = (cudaStream_t)stream;
+    char *host = (char *)host_out;
+    uint64_t c = 0;
+    for (uint64_t i0 = 0; i0 < nper && s == PRAND_OK; i0 += k) {
+        const uint64_t kk = std::min(k, nper - i0);
+        StreamRange proto;
+        proto.stride = n;
+        const uint32_t idx0 = h->mt_idx;
+        uint32_t idx_next = idx0;
+        for (uint64_t j0 = 0; j0 < n && s == PRAND_OK; j0 += cs, ++c) {
+            const uint64_t cnt = std::min(cs, n - j0);
+            const int b = (int)(c & 1);
+            if (c >= 2 && cudaStreamWaitEvent(st, h->ev_copy[b], 0) != cudaSuccess) { s = PRAND_ERR_CUDA; break; }
+            void *dst = h->stage[b];
+            if (h->gen == PRAND_MT19937) {
+                uint32_t idx = idx0;
+                s = mt_gen((uint32_t *)h->d_state + j0 * kMtN, cnt, &idx, dst, dtype, kk, st);
+                idx_next = idx;
+            } else {
+                StreamRange R = proto;
+                R.j0 = j0;
+                R.count = cnt;
+                if (is_gm(h->gen)) s = gm_gen(h->gen, h->T, h->d_state, h->d_spare, R, dst, dtype, kk, st);
+                else s = mrg_lfsr_gen(h->gen, h->T, h->d_state, h->d_spare, R, dst, dtype, kk, st);
+                proto.nsec = R.nsec;
+                proto.seclen = R.seclen;
+            }
+            if (s != PRAND_OK) break;
+            char *hdst = host + (j0 * nper + i0) * esz;
+            if (cudaEventRecord(h->ev_gen[b], st) != cudaSuccess ||
+                cudaStreamWaitEvent(h->copy_st, h->ev_gen[b], 0) != cudaSuccess) {
+                s = PRAND_ERR_CUDA;
+                break;
+            }
+            // whole rows are one contiguous piece of host_out; partial rows are strided
+            const cudaError_t ce =
+                kk == nper ? cudaMemcpyAsync(hdst, dst, cnt * kk * esz, cudaMemcpyDeviceToHost, h->copy_st)
+                           : cudaMemcpy2DAsync(hdst, nper * esz, dst, kk * esz, kk * esz, cnt, cudaMemcpyDeviceToHost,
+                                               h->copy_st);
+            if (ce != cudaSuccess || cudaEventRecord(h->ev_copy[b], h->copy_st) != cudaSuccess) s = PRAND_ERR_CUDA;
+        }
+        if (s != PRAND_OK) break;
+        h->mt_idx = idx_next;
+        if (proto.nsec > 1) { void *t = h->d_state; h->d_state = h->d_spare; h->d_spare = t; }
+        h->position += kk;
+    }
+    // the copies into host_out are complete (or abandoned) before returning
+    if (cudaStreamSynchronize(h->copy_st) != cudaSuccess && s == PRAND_OK) s = PRAND_ERR_CUDA;
+    h->last_stream = st;
+    return s;
 }
 
 }  // namespace
@@ -244,6 +346,21 @@ prand_status_t prand_generate_f32(prand_handle_t h, float *dev_out, uint64_t n_p
 prand_status_t prand_generate_f64(prand_handle_t h, double *dev_out, uint64_t n_per_stream, prand_stream_t stream)
 {
     return generate_any(h, dev_out, PRAND_DTYPE_F64, n_per_stream, stream);
+}
+
+prand_status_t prand_generate_host_u32(prand_handle_t h, uint32_t *host_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_host(h, host_out, PRAND_DTYPE_U32, n_per_stream, stream);
+}
+
+prand_status_t prand_generate_host_f32(prand_handle_t h, float *host_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_host(h, host_out, PRAND_DTYPE_F32, n_per_stream, stream);
+}
+
+prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint64_t n_per_stream, prand_stream_t stream)
+{
+    return generate_host(h, host_out, PRAND_DTYPE_F64, n_per_stream, stream);
 }
 
 prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4])
@@ -329,6 +446,7 @@ prand_status_t prand_destroy(prand_handle_t h)
     if (prev != h->device) cudaSetDevice(h->device);
     cudaStreamSynchronize(h->last_stream);
     free_states(h);
+    free_staging(h);
     if (h->d_base) cudaFree(h->d_base);
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     delete h;

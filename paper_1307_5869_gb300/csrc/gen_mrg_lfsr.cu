@@ -70,7 +70,7 @@ __global__ void mrg_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t n
 // no thread reads a state that another thread has already replaced).
 template <typename OutT, bool ROWS = false>
 __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
-                                                      uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                      uint64_t stride, uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                       OutT *__restrict__ out, int vec)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
         const uint64_t len = (live && start < nper) ? min(seclen, nper - start) : 0;
         uint32_t x0 = 0, x1 = 0, x2 = 0, y0 = 0, y1 = 0, y2 = 0;
         if (len) {
-            x0 = state[j]; x1 = state[nstreams + j]; x2 = state[2 * nstreams + j];
-            y0 = state[3 * nstreams + j]; y1 = state[4 * nstreams + j]; y2 = state[5 * nstreams + j];
+            x0 = state[j]; x1 = state[stride + j]; x2 = state[2 * stride + j];
+            y0 = state[3 * stride + j]; y1 = state[4 * stride + j]; y2 = state[5 * stride + j];
             if (start) {
                 uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
                 for (int b = 0; b < 64; ++b)
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
                         [](uint32_t u) { return Cvt<OutT, true>::f(u); }, out + j * nper + start, len,
                         tiles[threadIdx.x >> 5], threadIdx.x & 31);
         if (len && start + len == nper) {
-            sout[j] = x0; sout[nstreams + j] = x1; sout[2 * nstreams + j] = x2;
-            sout[3 * nstreams + j] = y0; sout[4 * nstreams + j] = y1; sout[5 * nstreams + j] = y2;
+            sout[j] = x0; sout[stride + j] = x1; sout[2 * stride + j] = x2;
+            sout[3 * stride + j] = y0; sout[4 * stride + j] = y1; sout[5 * stride + j] = y2;
         }
         return;
     }
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
     uint64_t start = (uint64_t)sec * seclen;
     if (start >= nper) return;
     uint64_t len = min(seclen, nper - start);
-    uint32_t x0 = state[j], x1 = state[nstreams + j], x2 = state[2 * nstreams + j];
-    uint32_t y0 = state[3 * nstreams + j], y1 = state[4 * nstreams + j], y2 = state[5 * nstreams + j];
+    uint32_t x0 = state[j], x1 = state[stride + j], x2 = state[2 * stride + j];
+    uint32_t y0 = state[3 * stride + j], y1 = state[4 * stride + j], y2 = state[5 * stride + j];
     if (start) {
         uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
         for (int b = 0; b < 64; ++b)
@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
     }
     for (; i < len; ++i) o[i] = Cvt<OutT, true>::f(mrg_next(x0, x1, x2, y0, y1, y2));
     if (start + len == nper) {
-        sout[j] = x0; sout[nstreams + j] = x1; sout[2 * nstreams + j] = x2;
-        sout[3 * nstreams + j] = y0; sout[4 * nstreams + j] = y1; sout[5 * nstreams + j] = y2;
+        sout[j] = x0; sout[stride + j] = x1; sout[2 * stride + j] = x2;
+        sout[3 * stride + j] = y0; sout[4 * stride + j] = y1; sout[5 * stride + j] = y2;
     }
 }
 
@@ -191,7 +191,7 @@ __global__ void lfsr_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t 
 
 template <typename OutT, bool ROWS = false>
 __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
-                                                       uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                       uint64_t stride, uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                        OutT *__restrict__ out, int vec)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restric
         const uint64_t len = (live && start < nper) ? min(seclen, nper - start) : 0;
         uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;
         if (len) {
-            z0 = state[j]; z1 = state[nstreams + j]; z2 = state[2 * nstreams + j]; z3 = state[3 * nstreams + j];
+            z0 = state[j]; z1 = state[stride + j]; z2 = state[2 * stride + j]; z3 = state[3 * stride + j];
             if (start) {
                 uint32_t z[4] = { z0, z1, z2, z3 };
                 for (int b = 0; b < 64; ++b)
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restric
         fill_rows<OutT>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
                         out + j * nper + start, len, tiles[threadIdx.x >> 5], threadIdx.x & 31);
         if (len && start + len == nper) {
-            sout[j] = z0; sout[nstreams + j] = z1; sout[2 * nstreams + j] = z2; sout[3 * nstreams + j] = z3;
+            sout[j] = z0; sout[stride + j] = z1; sout[2 * stride + j] = z2; sout[3 * stride + j] = z3;
         }
         return;
     }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restric
     uint64_t start = (uint64_t)sec * seclen;
     if (start >= nper) return;
     uint64_t len = min(seclen, nper - start);
-    uint32_t z0 = state[j], z1 = state[nstreams + j], z2 = state[2 * nstreams + j], z3 = state[3 * nstreams + j];
+    uint32_t z0 = state[j], z1 = state[stride + j], z2 = state[2 * stride + j], z3 = state[3 * stride + j];
     if (start) {
         uint32_t z[4] = { z0, z1, z2, z3 };
         for (int b = 0; b < 64; ++b)
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restric
     }
     for (; i < len; ++i) o[i] = Cvt<OutT>::f(lfsr_next(z0, z1, z2, z3));
     if (start + len == nper) {
-        sout[j] = z0; sout[nstreams + j] = z1; sout[2 * nstreams + j] = z2; sout[3 * nstreams + j] = z3;
+        sout[j] = z0; sout[stride + j] = z1; sout[2 * stride + j] = z2; sout[3 * stride + j] = z3;
     }
 }
 
@@ -310,38 +310,37 @@ static void pick_sections(uint64_t nstreams, uint64_t nper, uint32_t *nsec, uint
 }
 
 template <typename OutT>
-static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams,
-                                     OutT *out, uint64_t nper, cudaStream_t st, bool *swapped)
+static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R,
+                                     OutT *out, uint64_t nper, cudaStream_t st)
 {
-    uint32_t nsec;
-    uint64_t seclen;
-    pick_sections(nstreams, nper, &nsec, &seclen);
+    if (R.nsec == 0) pick_sections(R.count, nper, &R.nsec, &R.seclen);
+    const uint32_t nsec = R.nsec;
+    const uint64_t seclen = R.seclen, nstreams = R.count;
     int vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0;
     const unsigned B = 256;
     uint64_t threads = nstreams * nsec;
-    uint32_t *sin = (uint32_t *)d_state, *sout = nsec > 1 ? (uint32_t *)d_spare : sin;
-    *swapped = nsec > 1;
+    uint32_t *sin = (uint32_t *)d_state + R.j0, *sout = (nsec > 1 ? (uint32_t *)d_spare : (uint32_t *)d_state) + R.j0;
     // staged row stores need every row start 16-byte aligned
     constexpr uint64_t E = RowFill<OutT>::E;
     const bool rows = ((uintptr_t)out % 16) == 0 && nper % E == 0 && seclen % E == 0;
     if (gen == PRAND_MRG32K3A) {
-        if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
-        else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+        if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     } else {
-        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
-        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, nper, nsec, seclen, out, vec);
+        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     }
     return launch_check();
 }
 
-prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out,
-                            int dtype, uint64_t nper, cudaStream_t st, bool *swapped)
+prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out,
+                            int dtype, uint64_t nper, cudaStream_t st)
 {
     if (dtype == PRAND_DTYPE_U32)
-        return mrg_lfsr_gen_t<uint32_t>(gen, T, d_state, d_spare, nstreams, (uint32_t *)out, nper, st, swapped);
+        return mrg_lfsr_gen_t<uint32_t>(gen, T, d_state, d_spare, R, (uint32_t *)out, nper, st);
     if (dtype == PRAND_DTYPE_F32)
-        return mrg_lfsr_gen_t<float>(gen, T, d_state, d_spare, nstreams, (float *)out, nper, st, swapped);
-    return mrg_lfsr_gen_t<double>(gen, T, d_state, d_spare, nstreams, (double *)out, nper, st, swapped);
+        return mrg_lfsr_gen_t<float>(gen, T, d_state, d_spare, R, (float *)out, nper, st);
+    return mrg_lfsr_gen_t<double>(gen, T, d_state, d_spare, R, (double *)out, nper, st);
 }
 
 }  // namespace prand
@@ -425,8 +424,8 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     int vec = ((uintptr_t)dev_out % 16) == 0;
     const unsigned B = 256;
     uint32_t *sout = nsec > 1 ? D->next : dev_state;
-    mrg_gen_kernel<uint32_t><<<grid_for(n_streams * nsec, B), B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_per_stream,
-                                                                          nsec, seclen, dev_out, vec);
+    mrg_gen_kernel<uint32_t><<<grid_for(n_streams * nsec, B), B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_streams,
+                                                                          n_per_stream, nsec, seclen, dev_out, vec);
     if ((s = launch_check()) != PRAND_OK) return s;
     if (nsec > 1) {
         mrg_copy_words_kernel<<<grid_for(6 * n_streams, B), B, 0, st>>>(D->next, dev_state, 6 * n_streams);

@@ -8,42 +8,42 @@ prand_status_t gm19_table(uint64_t *, cudaStream_t);
 prand_status_t gm19_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gm19_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gm19_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gm19_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gm19_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gm29_table(uint64_t *, cudaStream_t);
 prand_status_t gm29_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gm29_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gm29_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gm29_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gm29_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gm31_table(uint64_t *, cudaStream_t);
 prand_status_t gm31_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gm31_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gm31_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gm31_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gm31_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gm55_table(uint64_t *, cudaStream_t);
 prand_status_t gm55_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gm55_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gm55_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gm55_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gm55_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gm61_table(uint64_t *, cudaStream_t);
 prand_status_t gm61_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gm61_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gm61_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gm61_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gm61_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gq58_1_table(uint64_t *, cudaStream_t);
 prand_status_t gq58_1_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gq58_1_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gq58_1_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gq58_1_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gq58_1_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gq58_3_table(uint64_t *, cudaStream_t);
 prand_status_t gq58_3_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gq58_3_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gq58_3_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gq58_3_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gq58_3_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 prand_status_t gq58_4_table(uint64_t *, cudaStream_t);
 prand_status_t gq58_4_seed(const uint64_t *, uint64_t *, uint64_t, cudaStream_t);
 prand_status_t gq58_4_init(const uint64_t *, const uint64_t *, uint64_t *, uint64_t, uint64_t, cudaStream_t);
 prand_status_t gq58_4_skip(const uint64_t *, uint64_t *, uint64_t, const U256 &, cudaStream_t);
-prand_status_t gq58_4_gen(const uint64_t *, uint64_t *, uint64_t *, uint64_t, void *, int, uint64_t, cudaStream_t, bool *);
+prand_status_t gq58_4_gen(const uint64_t *, uint64_t *, uint64_t *, StreamRange &, void *, int, uint64_t, cudaStream_t);
 
 static const GmParams kGmHost[8] = {
     { 15, 28, (1ull << 19) - 1, 0, 1, 32, 32, P19, 6000000ull, 1000ull },
@@ -128,20 +128,20 @@ prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, c
     }
 }
 
-prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, uint64_t nstreams, void *out, int dtype,
-                      uint64_t nper, cudaStream_t st, bool *swapped)
+prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out, int dtype,
+                      uint64_t nper, cudaStream_t st)
 {
     const uint64_t *tab = T->gm[gen - PRAND_GM19];
     uint64_t *s = (uint64_t *)d_state, *sp = (uint64_t *)d_spare;
     switch (gen) {
-    case PRAND_GM19: return gm19_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GM29: return gm29_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GM31: return gm31_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GM55: return gm55_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GM61: return gm61_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GQ58_1: return gq58_1_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GQ58_3: return gq58_3_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
-    case PRAND_GQ58_4: return gq58_4_gen(tab, s, sp, nstreams, out, dtype, nper, st, swapped);
+    case PRAND_GM19: return gm19_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GM29: return gm29_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GM31: return gm31_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GM55: return gm55_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GM61: return gm61_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GQ58_1: return gq58_1_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GQ58_3: return gq58_3_gen(tab, s, sp, R, out, dtype, nper, st);
+    case PRAND_GQ58_4: return gq58_4_gen(tab, s, sp, R, out, dtype, nper, st);
     default: return PRAND_ERR_ARG;
     }
 }

@@ -380,8 +380,9 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, 
 // group has already replaced).
 template <int GEN, typename OutT, bool VEC>
 __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
-                                                     uint64_t *state_out, uint64_t nstreams, uint64_t nper,
-                                                     uint32_t nsec, uint64_t seclen, OutT *__restrict__ out)
+                                                     uint64_t *state_out, uint64_t nstreams, uint64_t stride,
+                                                     uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                     OutT *__restrict__ out)
 {
     using P = GmT<GEN>;
     constexpr int G = P::lanes;
@@ -398,13 +399,13 @@ __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict_
     uint64_t zp = 0, zc = 0;
     if (pt) {
         zp = state_in[j * P::s + li] >> P::t;
-        zc = state_in[(nstreams + j) * P::s + li] >> P::t;
+        zc = state_in[(stride + j) * P::s + li] >> P::t;
         if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
     }
     gm_generate_section<GEN, OutT, VEC>(zc, zp, pt, li, gmask, out + j * nper + start, len, slots + 4 * threadIdx.x);
     if (pt && start + len == nper) {
         state_out[j * P::s + li] = gm_canon<GEN>(zp) << P::t;
-        state_out[(nstreams + j) * P::s + li] = gm_canon<GEN>(zc) << P::t;
+        state_out[(stride + j) * P::s + li] = gm_canon<GEN>(zc) << P::t;
     }
 }
 
@@ -438,34 +439,44 @@ struct GmHost {
         gm_skip_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, state, n, off);
         return launch_check();
     }
-    template <typename OutT>
-    static prand_status_t gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, uint64_t nstreams, OutT *out,
-                              uint64_t nper, cudaStream_t st, bool *swapped)
+    // Sections per stream: groups to fill the GPU (64 resident warps per SM
+    // worth of lanes), section starts on multiples of 4 G outputs.
+    static void pick(uint64_t nstreams, uint64_t nper, uint32_t *nsec, uint64_t *seclen)
     {
         constexpr int G = GmT<GEN>::lanes;
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // groups to fill the GPU: 64 resident warps per SM worth of lanes
         uint64_t target = (uint64_t)sms * 64 * (32 / G);
         uint64_t s = nstreams < target ? (target + nstreams - 1) / nstreams : 1;
         uint64_t maxs = nper / (16 * G) ? nper / (16 * G) : 1;
         if (s > maxs) s = maxs;
         if (s > 65535) s = 65535;
-        uint64_t seclen = (nper + s - 1) / s;
-        seclen = (seclen + 4 * G - 1) / (4 * G) * (4 * G);
-        if (seclen == 0) seclen = 4 * G;
-        uint32_t nsec = (uint32_t)((nper + seclen - 1) / seclen);
-        if (nsec == 0) nsec = 1;
+        uint64_t len = (nper + s - 1) / s;
+        len = (len + 4 * G - 1) / (4 * G) * (4 * G);
+        if (len == 0) len = 4 * G;
+        *seclen = len;
+        *nsec = (uint32_t)((nper + len - 1) / len);
+        if (*nsec == 0) *nsec = 1;
+    }
+    template <typename OutT>
+    static prand_status_t gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, StreamRange &R, OutT *out,
+                              uint64_t nper, cudaStream_t st)
+    {
+        constexpr int G = GmT<GEN>::lanes;
+        if (R.nsec == 0) pick(R.count, nper, &R.nsec, &R.seclen);
+        const uint32_t nsec = R.nsec;
+        const uint64_t seclen = R.seclen, nstreams = R.count;
         // section starts are multiples of 4 G, so rows start 16-byte aligned when
         // the output is aligned and n_per_stream is a multiple of 4
         const bool vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0 && nper % 4 == 0;
         const unsigned B = 256;
-        uint64_t *sout = nsec > 1 ? spare : state;
-        *swapped = nsec > 1;
+        const uint64_t off = R.j0 * GmT<GEN>::s;
+        const uint64_t *sin = state + off;
+        uint64_t *sout = (nsec > 1 ? spare : state) + off;
         const unsigned grid = gm_grid_for(nstreams * nsec * G, B);
-        if (vec) gm_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, state, sout, nstreams, nper, nsec, seclen, out);
-        else gm_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, state, sout, nstreams, nper, nsec, seclen, out);
+        if (vec) gm_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+        else gm_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
         return launch_check();
     }
 };
@@ -488,14 +499,14 @@ struct GmHost {
     {                                                                                                         \
         return GmHost<GEN>::skip(tab, state, n, off, st);                                                     \
     }                                                                                                         \
-    prand_status_t NAME##_gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, uint64_t nstreams,       \
-                              void *out, int dtype, uint64_t nper, cudaStream_t st, bool *sw)                  \
+    prand_status_t NAME##_gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, StreamRange &R,          \
+                              void *out, int dtype, uint64_t nper, cudaStream_t st)                            \
     {                                                                                                         \
         if (dtype == PRAND_DTYPE_U32)                                                                         \
-            return GmHost<GEN>::template gen<uint32_t>(tab, state, spare, nstreams, (uint32_t *)out, nper, st, sw); \
+            return GmHost<GEN>::template gen<uint32_t>(tab, state, spare, R, (uint32_t *)out, nper, st); \
         if (dtype == PRAND_DTYPE_F32)                                                                         \
-            return GmHost<GEN>::template gen<float>(tab, state, spare, nstreams, (float *)out, nper, st, sw);  \
-        return GmHost<GEN>::template gen<double>(tab, state, spare, nstreams, (double *)out, nper, st, sw);    \
+            return GmHost<GEN>::template gen<float>(tab, state, spare, R, (float *)out, nper, st);  \
+        return GmHost<GEN>::template gen<double>(tab, state, spare, R, (double *)out, nper, st);    \
     }
 
 }  // namespace prand

@@ -89,6 +89,43 @@ prand_status_t launch_check();  // cudaGetLastError after a launch; counts it
 // Offsets as 256-bit little-endian numbers.
 struct U256 { uint64_t w[4]; };
 
+// The streams one fill covers: streams j0 .. j0 + count - 1 of state arrays
+// laid out for `stride` streams.  Sections: nsec == 0 lets the family choose
+// (nsec and seclen are written back); otherwise the given pair is used, so the
+// fills of several ranges in one call split their streams alike and keep their
+// next states in the same buffer (in place when nsec == 1, the spare otherwise).
+struct StreamRange {
+    uint64_t stride = 0, j0 = 0, count = 0;
+    uint32_t nsec = 0;
+    uint64_t seclen = 0;
+};
+
+// Family entry points (gen_mrg_lfsr.cu, gm_dispatch.cpp, gen_mt.cu), all
+// asynchronous on `st`.  The *_gen functions fill `out` (stream-major, R.count
+// rows of nper) from the streams of R and leave their next states in place or,
+// when R.nsec > 1, in the spare buffer (the caller swaps the two afterwards).
+prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st);
+prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st);
+prand_status_t gm_build_table(int gen, uint64_t *tab, cudaStream_t st);
+prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                             cudaStream_t st);
+prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
+prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out,
+                            int dtype, uint64_t nper, cudaStream_t st);
+prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
+                       cudaStream_t st);
+prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
+prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out, int dtype,
+                      uint64_t nper, cudaStream_t st);
+prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
+prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st);
+// MT19937 keeps its state as 624-word blocks per stream (a range is a pointer
+// offset); *idx, the position inside the block shared by all streams, advances.
+prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
+
 // Family-specific device work, all asynchronous on `st` unless noted.
 // Base state of one "stream" in the family's device layout.
 prand_status_t seed_base(int gen, uint64_t seed, void *d_base, cudaStream_t st);
