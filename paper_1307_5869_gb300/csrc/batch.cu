@@ -153,7 +153,7 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
     uint32_t idx = kMtN;
     if (T.flags & kTileFromSlot) {
         const uint32_t *src = (const uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.slot;
-        for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
+        mt_copy_state_warp(src, b0, lane);
         idx = src[kMtN];
         __syncwarp();
     } else {
@@ -166,7 +166,7 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
             __syncwarp();
         }
         if (first) {
-            for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
+            mt_copy_state_warp(src, b0, lane);
             __syncwarp();
         }
     }
@@ -198,7 +198,7 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
     if (T.flags & kTileLast) {
         const uint32_t *cur = in_b0 ? b0 : b1;
         uint32_t *d = (uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.wslot;
-        for (int i = lane; i < kMtN; i += 32) d[i] = cur[i];
+        mt_copy_state_warp(cur, d, lane);
         if (lane == 0) d[kMtN] = idx;
     }
     __syncwarp();

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_gen_kernel(uint32_t 
     if (j >= nstreams) return;  // whole warp
     uint32_t *b0 = sm[w][0], *b1 = sm[w][1];
     const uint32_t *src = state + j * kMtN;
-    for (int i = lane; i < kMtN; i += 32) b0[i] = src[i];
+    mt_copy_state_warp(src, b0, lane);
     __syncwarp();
     OutT *o = out + j * nper;
     uint64_t done = 0;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_gen_kernel(uint32_t 
     }
     const uint32_t *cur = in_b0 ? b0 : b1;
     uint32_t *dst = state + j * kMtN;
-    for (int i = lane; i < kMtN; i += 32) dst[i] = cur[i];
+    mt_copy_state_warp(cur, dst, lane);
 }
 
 // ------------------------------------------------------------------ jump

@@ -13,6 +13,25 @@ __device__ __forceinline__ uint32_t mt_recur(uint32_t xt, uint32_t xt1, uint32_t
     return xt397 ^ (y >> 1) ^ ((y & 1u) ? 0x9908B0DFu : 0u);
 }
 
+// Copy one 624-word state with a warp: all of a lane's 20 loads are issued
+// before any of its stores, so the copy costs one memory latency rather than
+// twenty.  Each lane moves its own words (src and dst may be the same buffer).
+__device__ __forceinline__ void mt_copy_state_warp(const uint32_t *src, uint32_t *dst, int lane)
+{
+    constexpr int R = (kMtN + 31) / 32;  // 20
+    uint32_t r[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        r[k] = i < kMtN ? src[i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = lane + 32 * k;
+        if (i < kMtN) dst[i] = r[k];
+    }
+}
+
 __device__ __forceinline__ uint32_t mt_temper(uint32_t y)
 {
     y ^= y >> 11;
@@ -94,7 +113,7 @@ __device__ inline void mt_apply_poly_warp(const uint32_t *__restrict__ poly, con
     uint32_t acc[W], win[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
-    for (int i = lane; i < kMtN; i += 32) seq[i] = src[i];  // each lane copies its own words (src may be seq)
+    mt_copy_state_warp(src, seq, lane);
     __syncwarp();
     mt_twist_block(seq, seq + kMtN, lane);  // block 1 into slot 1
 #pragma unroll
