@@ -362,7 +362,7 @@ prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTable
     if ((s = engine_bases(*E, seed, st, &B)) != PRAND_OK) return s;
     memset(ctx, 0, sizeof *ctx);
     ctx->mrg_tab = E->T->mrg;
-    ctx->lfsr_tab = E->T->lfsr;
+    ctx->lfsr_tab = E->T->lfsr4;
     ctx->mt_polys = E->T->mt;
     for (int g = 0; g < 8; ++g) ctx->gm_tab[g] = E->T->gm[g];
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) ctx->base[g] = (const char *)B->dev + B->off[g];

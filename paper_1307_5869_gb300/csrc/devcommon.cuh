@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "prand_internal.h"
 
 namespace prand {
@@ -240,6 +242,27 @@ __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, ui
         }
         __syncwarp();
     }
+}
+
+// Resident threads of a 256-thread kernel on the current device, computed once
+// per kernel and device (ID tells the kernels apart).
+template <int ID, typename K>
+inline uint64_t resident_threads(K kernel)
+{
+    constexpr int kDevs = 64;
+    static std::atomic<uint64_t> cache[kDevs];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < kDevs) {
+        const uint64_t c = cache[dev].load(std::memory_order_relaxed);
+        if (c) return c;
+    }
+    int sms = 152, bps = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, 0) != cudaSuccess || bps < 1) bps = 1;
+    const uint64_t c = (uint64_t)sms * bps * 256;
+    if (dev >= 0 && dev < kDevs) cache[dev].store(c, std::memory_order_relaxed);
+    return c;
 }
 
 // Big offsets.

@@ -7,6 +7,8 @@
 // GF(2) powers of the LFSR word step), exactly as the paper's array fill
 // splits an array into sections (Sec. 6).  State is stored structure-of-arrays
 // (word c of stream j at state[c * nstreams + j]) so a warp loads it coalesced.
+#include <atomic>
+
 #include "mrg_lfsr_dev.cuh"
 
 namespace prand {
@@ -148,6 +150,19 @@ __global__ void lfsr_table_kernel(uint32_t *tab)
     }
 }
 
+// Nibble tables from the column tables: one thread per entry.
+__global__ void lfsr_table4_kernel(const uint32_t *tab, uint32_t *tab4)
+{
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 4u * kJumpBits * 128u) return;
+    const uint32_t v = id & 15u, k = (id >> 4) & 7u, cb = id >> 7;  // cb = c * kJumpBits + b
+    const uint32_t *col = tab + (size_t)cb * 32;
+    uint32_t r = 0;
+    for (int i = 0; i < 4; ++i)
+        if ((v >> i) & 1u) r ^= col[4 * k + i];
+    tab4[id] = r;
+}
+
 // Default state: 987654321 in all four words (L'Ecuyer's example seed; the paper
 // prints none).  Seeded: the high 32 bits of SplitMix64 draws, redrawn while
 // the top p bits of a component are all zero.
@@ -256,9 +271,14 @@ prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st)
     return launch_check();
 }
 
+// tab: [4][kJumpBits][32] column images, then tab4 = tab + 4 * kJumpBits * 32:
+// [4][kJumpBits][8][16] nibble tables (the form the jumps use).
 prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st)
 {
     lfsr_table_kernel<<<1, 32, 0, st>>>(tab);
+    prand_status_t s = launch_check();
+    if (s != PRAND_OK) return s;
+    lfsr_table4_kernel<<<(4 * kJumpBits * 128 + 255) / 256, 256, 0, st>>>(tab, tab + 4 * kJumpBits * 32);
     return launch_check();
 }
 
@@ -276,7 +296,7 @@ prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, vo
     if (gen == PRAND_MRG32K3A)
         mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
     else
-        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr4, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
     return launch_check();
 }
 
@@ -284,36 +304,36 @@ prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_
 {
     const unsigned B = 128;
     if (gen == PRAND_MRG32K3A) mrg_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (uint32_t *)d_state, n, off);
-    else lfsr_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (uint32_t *)d_state, n, off);
+    else lfsr_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr4, (uint32_t *)d_state, n, off);
     return launch_check();
 }
 
-// Sections per stream: enough threads to fill the GPU (about 8 resident warps
-// of work per SM scheduler), sections no shorter than 256 outputs.
-static void pick_sections(uint64_t nstreams, uint64_t nper, uint32_t *nsec, uint64_t *seclen)
+// Sections per stream: whole waves of the kernel's resident threads (cap),
+// sections no shorter than 256 outputs and starting on multiples of 32
+// outputs, so the staged 128-byte row stores of every section fill whole
+// cache lines.
+static void pick_sections(uint64_t nstreams, uint64_t nper, uint64_t cap, uint32_t *nsec, uint64_t *seclen)
 {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    uint64_t target = (uint64_t)sms * 2048;
-    uint64_t s = 1;
-    if (nstreams < target) s = (target + nstreams - 1) / nstreams;
-    uint64_t maxs = nper / 256 ? nper / 256 : 1;
-    if (s > maxs) s = maxs;
-    if (s > 65535) s = 65535;
+    const uint32_t s = pick_nsec(nstreams, cap, nper / 256, nper);
     uint64_t len = (nper + s - 1) / s;
-    len = (len + 3) & ~3ull;  // keep section starts 4-aligned for vector stores
-    if (len == 0) len = 4;
+    len = (len + 31) & ~31ull;
+    if (len == 0) len = 32;
     *seclen = len;
     *nsec = (uint32_t)((nper + len - 1) / len);
     if (*nsec == 0) *nsec = 1;
 }
 
+
 template <typename OutT>
 static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R,
                                      OutT *out, uint64_t nper, cudaStream_t st)
 {
-    if (R.nsec == 0) pick_sections(R.count, nper, &R.nsec, &R.seclen);
+    if (R.nsec == 0) {
+        // size by the rows form (the other form has the same footprint or less)
+        const uint64_t cap = gen == PRAND_MRG32K3A ? resident_threads<1>(mrg_gen_kernel<OutT, true>)
+                                                   : resident_threads<2>(lfsr_gen_kernel<OutT, true>);
+        pick_sections(R.count, nper, cap, &R.nsec, &R.seclen);
+    }
     const uint32_t nsec = R.nsec;
     const uint64_t seclen = R.seclen, nstreams = R.count;
     int vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0;
@@ -327,8 +347,8 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
         if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
         else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     } else {
-        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
-        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr4, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr4, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     }
     return launch_check();
 }
@@ -420,7 +440,7 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     if (n_per_stream == 0) return PRAND_OK;
     uint32_t nsec;
     uint64_t seclen;
-    pick_sections(n_streams, n_per_stream, &nsec, &seclen);
+    pick_sections(n_streams, n_per_stream, resident_threads<3>(mrg_gen_kernel<uint32_t>), &nsec, &seclen);
     int vec = ((uintptr_t)dev_out % 16) == 0;
     const unsigned B = 256;
     uint32_t *sout = nsec > 1 ? D->next : dev_state;

@@ -439,19 +439,12 @@ struct GmHost {
         gm_skip_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, state, n, off);
         return launch_check();
     }
-    // Sections per stream: groups to fill the GPU (64 resident warps per SM
-    // worth of lanes), section starts on multiples of 4 G outputs.
-    static void pick(uint64_t nstreams, uint64_t nper, uint32_t *nsec, uint64_t *seclen)
+    // Sections per stream: whole waves of the kernel's resident lane groups
+    // (cap), section starts on multiples of 4 G outputs.
+    static void pick(uint64_t nstreams, uint64_t nper, uint64_t cap, uint32_t *nsec, uint64_t *seclen)
     {
         constexpr int G = GmT<GEN>::lanes;
-        int dev = 0, sms = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        uint64_t target = (uint64_t)sms * 64 * (32 / G);
-        uint64_t s = nstreams < target ? (target + nstreams - 1) / nstreams : 1;
-        uint64_t maxs = nper / (16 * G) ? nper / (16 * G) : 1;
-        if (s > maxs) s = maxs;
-        if (s > 65535) s = 65535;
+        const uint32_t s = pick_nsec(nstreams, cap, nper / (16 * G), nper);
         uint64_t len = (nper + s - 1) / s;
         len = (len + 4 * G - 1) / (4 * G) * (4 * G);
         if (len == 0) len = 4 * G;
@@ -464,7 +457,8 @@ struct GmHost {
                               uint64_t nper, cudaStream_t st)
     {
         constexpr int G = GmT<GEN>::lanes;
-        if (R.nsec == 0) pick(R.count, nper, &R.nsec, &R.seclen);
+        if (R.nsec == 0)
+            pick(R.count, nper, resident_threads<GEN>(gm_gen_kernel<GEN, OutT, true>) / G, &R.nsec, &R.seclen);
         const uint32_t nsec = R.nsec;
         const uint64_t seclen = R.seclen, nstreams = R.count;
         // section starts are multiples of 4 G, so rows start 16-byte aligned when

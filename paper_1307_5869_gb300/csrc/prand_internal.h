@@ -63,6 +63,7 @@ struct DevTables {
     int device = -1;
     uint32_t *mrg = nullptr;      // [kJumpBits][18]: A^(2^b) mod m1 (9 words), B^(2^b) mod m2 (9 words)
     uint32_t *lfsr = nullptr;     // [4][kJumpBits][32]: column images of T_c^(2^b)
+    uint32_t *lfsr4 = nullptr;    // [4][kJumpBits][8][16]: the same maps as nibble tables (jumps use these)
     uint64_t *gm[8] = {};         // per GM/GQ generator: [kJumpBits][4] = M^(2^b) mod p
     uint32_t *mt = nullptr;       // [kMtPolyCount][kMtPolyWords]: x^(2^b) mod phi
     bool ready_basic = false;
@@ -99,6 +100,34 @@ struct StreamRange {
     uint32_t nsec = 0;
     uint64_t seclen = 0;
 };
+
+// Sections per stream for a launch of `units` work items (threads or lane
+// groups, one per stream) with nper outputs each, when `cap` items are
+// resident at once: the count in [1, max_s] whose grid best fills whole waves,
+// discounted for the fixed work each section starts with (its jump, state
+// load and store: about 128 outputs' worth).  Candidates: 1..64, multiples of one wave's worth, max_s.
+inline uint32_t pick_nsec(uint64_t units, uint64_t cap, uint64_t max_s, uint64_t nper)
+{
+    if (cap == 0 || units == 0 || nper == 0) return 1;
+    if (max_s < 1) max_s = 1;
+    if (max_s > 65535) max_s = 65535;
+    auto score = [&](uint64_t s) {
+        const uint64_t n = units * s, waves = (n + cap - 1) / cap;
+        return ((double)n / (double)(waves * cap)) / (1.0 + 128.0 * (double)s / (double)nper);
+    };
+    uint64_t best = 1;
+    double best_score = score(1);
+    auto consider = [&](uint64_t s) {
+        if (s < 1 || s > max_s) return;
+        const double v = score(s);
+        if (v > best_score + 1e-9) { best_score = v; best = s; }
+    };
+    for (uint64_t s = 2; s <= 64; ++s) consider(s);
+    const uint64_t wave = (cap + units - 1) / units;  // sections per stream for one full wave
+    for (uint64_t k = 1; k <= 8; ++k) consider(k * wave);
+    consider(max_s);
+    return (uint32_t)best;
+}
 
 // Family entry points (gen_mrg_lfsr.cu, gm_dispatch.cpp, gen_mt.cu), all
 // asynchronous on `st`.  The *_gen functions fill `out` (stream-major, R.count
