@@ -45,27 +45,29 @@ __device__ __forceinline__ uint32_t mt_temper(uint32_t y)
 // memory) fused with the tempered output: every new word is tempered and
 // stored straight from registers while it is written to the new block.  New
 // word k reads old words k, k+1 (new word 0 for k = 623) and old word k + 397
-// (k < 227) or new word k - 227 (k >= 227, from a chunk at least 196 words
-// earlier).  So the block is made in 20 chunks of 32 words in order, with one
-// warp sync between chunks: no lane reads a word written in its own chunk, and
-// only the last chunk is partly empty.  Words k < emit are written to o[k];
-// FULL (emit == 624) drops that test.
+// (k < 227) or new word k - 227 (k >= 227).  So the block is made in 20 chunks
+// of 32 words in order.  The loop is unrolled completely so each chunk knows
+// its case at compile time (only chunk 7 mixes the two partner sources and
+// only chunk 19 is partly empty).  A word read from the new block was written
+// at least seven chunks earlier, so a warp sync every fourth chunk orders
+// every such read after its write.  Words k < emit are written to o[k]; FULL
+// (emit == 624) drops that test.
 template <typename OutT, bool FULL>
 __device__ __forceinline__ void mt_twist_emit_chunks(const uint32_t *__restrict__ ob, uint32_t *__restrict__ nb,
                                                      int lane, OutT *o, uint32_t emit)
 {
-#pragma unroll 4
+#pragma unroll
     for (int c = 0; c < 20; ++c) {
         const int k = 32 * c + lane;
-        if (k < kMtN) {
+        if (c < 19 || lane < kMtN - 32 * 19) {
             const uint32_t a = ob[k];
-            const uint32_t b = k + 1 < kMtN ? ob[k + 1] : nb[0];
-            const uint32_t p = k < 227 ? ob[k + 397] : nb[k - 227];
+            const uint32_t b = (c < 19 || lane < kMtN - 32 * 19 - 1) ? ob[k + 1] : nb[0];
+            const uint32_t p = c < 7 ? ob[k + 397] : c > 7 ? nb[k - 227] : (lane < 3 ? ob[k + 397] : nb[k - 227]);
             const uint32_t x = mt_recur(a, b, p);
             nb[k] = x;
             if (FULL || (uint32_t)k < emit) o[k] = Cvt<OutT>::f(mt_temper(x));
         }
-        __syncwarp();
+        if ((c & 3) == 3) __syncwarp();
     }
 }
 
@@ -81,15 +83,15 @@ __device__ __forceinline__ void mt_twist_emit(const uint32_t *__restrict__ ob, u
 // of mt_twist_emit_chunks.
 __device__ __forceinline__ void mt_twist_block(const uint32_t *ob, uint32_t *nb, int lane)
 {
-#pragma unroll 4
+#pragma unroll
     for (int c = 0; c < 20; ++c) {
         const int k = 32 * c + lane;
-        if (k < kMtN) {
-            const uint32_t b = k + 1 < kMtN ? ob[k + 1] : nb[0];
-            const uint32_t p = k < 227 ? ob[k + 397] : nb[k - 227];
+        if (c < 19 || lane < kMtN - 32 * 19) {
+            const uint32_t b = (c < 19 || lane < kMtN - 32 * 19 - 1) ? ob[k + 1] : nb[0];
+            const uint32_t p = c < 7 ? ob[k + 397] : c > 7 ? nb[k - 227] : (lane < 3 ? ob[k + 397] : nb[k - 227]);
             nb[k] = mt_recur(ob[k], b, p);
         }
-        __syncwarp();
+        if ((c & 3) == 3) __syncwarp();
     }
 }
 
