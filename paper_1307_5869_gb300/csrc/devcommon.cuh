@@ -133,11 +133,33 @@ __device__ __forceinline__ double u32_to_f64(uint32_t u)
     return __hiloint2double((int)hi, (int)lo);
 }
 
-// MRG32K3A f64 = z * RN(1 / (m1 + 1)): one round-to-nearest multiply.
+// MRG32K3A f64 = z * RN(1 / (m1 + 1)), one round-to-nearest multiply, done in
+// integer arithmetic so it stays off the FP64 pipe.  The constant is
+// M 2^-84 with M = 0x1000000D00000B (53 bits, high word 2^20), so the exact
+// product is P 2^-84 with P = z 2^52 + z Ml (Ml = M mod 2^32, one wide
+// multiply).  With top = P >> 32 of bit length L, the double keeps the 53 bits
+// P >> s, s = L - 21, rounded to nearest even on the s dropped bits, and its
+// bits are ((s + 990) << 52) + mantissa (a round-up to 2^53 carries into the
+// exponent by itself).  z = 0 gives 0.
 __device__ __forceinline__ double mrg_to_f64(uint32_t z)
 {
-    constexpr double kNorm = 1.0 / 4294967088.0;
-    return __dmul_rn((double)z, kNorm);
+    const uint64_t zm = (uint64_t)z * 0x0D00000Bu;               // z Ml < 2^60
+    const uint32_t w0 = (uint32_t)zm;                             // P mod 2^32
+    const uint64_t top = ((uint64_t)z << 20) + (zm >> 32);        // P >> 32 < 2^53
+    const uint32_t th = (uint32_t)(top >> 32), tl = (uint32_t)top;
+    const int L = th ? 64 - __clz(th) : 32 - __clz(tl);           // 21..53 for z >= 1
+    const int sh = L - 21;                                        // bits dropped, 0..32
+    uint32_t mlo, mhi;
+    asm("shf.r.clamp.b32 %0, %2, %3, %4;\n\t"
+        "shf.r.clamp.b32 %1, %3, %5, %4;"
+        : "=r"(mlo), "=r"(mhi) : "r"(w0), "r"(tl), "r"(sh), "r"(th));
+    // the dropped bits, left-aligned (0 when nothing is dropped); round up above
+    // one half, or at one half when the kept part is odd
+    const uint32_t rem = sh ? w0 << (32 - sh) : 0u;
+    const uint32_t up = rem > 0x80000000u - (mlo & 1u) ? 1u : 0u;
+    const uint64_t m = (((uint64_t)mhi << 32) | mlo) + up;
+    const uint64_t bits = ((uint64_t)(sh + 990) << 52) + m;
+    return z ? __longlong_as_double((long long)bits) : 0.0;
 }
 
 // ---------------------------------------------------------------- output

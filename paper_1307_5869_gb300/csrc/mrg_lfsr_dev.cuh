@@ -49,20 +49,50 @@ __device__ __forceinline__ void mrg_apply_bit(const uint32_t *tab, int b, uint32
     mat3_vec<22853>(tab + 18 * b + 9, y);
 }
 
-// One step of both components and the output z = (x - y) mod m1 in [1, m1].
-// x_{n+1} = 1403580 x_{n-1} - 810728 x_{n-2} (mod m1)
-// y_{n+1} = 527612 y_n - 1370589 y_{n-2}     (mod m2)
+// One MRG32K3A step (x_n = a x_{n-2} - b x_{n-3} mod m1, y_n = c y_{n-1} -
+// d y_{n-3} mod m2, Sec. 5.2) on canonical residues, in 32-bit limbs:
+// t = m - v (no borrow), S = A u + B t < 2^54 by two wide multiply-adds; with
+// 2^32 = e (mod m) (e = 209 or 22853) S folds to lo + e hi (for m2 twice,
+// the second high word being below 2^6); then r < 2^32 + 2^30 is made
+// canonical as r + e [r >= m], the condition being the carry out of r + e.
+// Returns z = x_n - y_n mod m1 in [1, m1].
 __device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_t &x2,
                                              uint32_t &y0, uint32_t &y1, uint32_t &y2)
 {
-    // signed difference of two < 2^53 products, shifted positive by a multiple of m
-    uint64_t u = (uint64_t)1403580u * x1 + (uint64_t)810728u * (uint64_t)kM1 - (uint64_t)810728u * x2;  // < 2^54
-    uint64_t r = (u & 0xFFFFFFFFull) + 209ull * (u >> 32);                                                 // < 2^32 + 2^30
-    uint32_t xn = (uint32_t)(r >= kM1 ? r - kM1 : r);
-    uint64_t w = (uint64_t)527612u * y0 + (uint64_t)1370589u * (uint64_t)kM2 - (uint64_t)1370589u * y2;   // < 2^54
-    uint64_t s = (w & 0xFFFFFFFFull) + 22853ull * (w >> 32);                                               // < 2^32 + 2^37
-    s = (s & 0xFFFFFFFFull) + 22853ull * (s >> 32);                                                        // < 2^32 + 2^20
-    uint32_t yn = (uint32_t)(s >= kM2 ? s - kM2 : s);
+    uint32_t xn, yn;
+    asm("{\n\t"
+        ".reg .u32 t, lo, hi, p, r, c, q;\n\t"
+        ".reg .u64 T, U;\n\t"
+        "sub.u32 t, 4294967087, %2;\n\t"
+        "mul.wide.u32 T, t, 810728;\n\t"
+        "mad.wide.u32 U, %1, 1403580, T;\n\t"
+        "mov.b64 {lo, hi}, U;\n\t"
+        "mul.lo.u32 p, hi, 209;\n\t"
+        "add.cc.u32 r, lo, p;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "add.cc.u32 q, r, 209;\n\t"
+        "addc.u32 c, c, 0;\n\t"
+        "mad.lo.u32 %0, c, 209, r;\n\t"
+        "}"
+        : "=r"(xn) : "r"(x1), "r"(x2));
+    asm("{\n\t"
+        ".reg .u32 t, lo, hi, s0, s1, p, r, c, q;\n\t"
+        ".reg .u64 T, W, S, L;\n\t"
+        "sub.u32 t, 4294944443, %2;\n\t"
+        "mul.wide.u32 T, t, 1370589;\n\t"
+        "mad.wide.u32 W, %1, 527612, T;\n\t"
+        "mov.b64 {lo, hi}, W;\n\t"
+        "cvt.u64.u32 L, lo;\n\t"
+        "mad.wide.u32 S, hi, 22853, L;\n\t"
+        "mov.b64 {s0, s1}, S;\n\t"
+        "mul.lo.u32 p, s1, 22853;\n\t"
+        "add.cc.u32 r, s0, p;\n\t"
+        "addc.u32 c, 0, 0;\n\t"
+        "add.cc.u32 q, r, 22853;\n\t"
+        "addc.u32 c, c, 0;\n\t"
+        "mad.lo.u32 %0, c, 22853, r;\n\t"
+        "}"
+        : "=r"(yn) : "r"(y0), "r"(y2));
     x2 = x1; x1 = x0; x0 = xn;
     y2 = y1; y1 = y0; y0 = yn;
     return xn > yn ? xn - yn : xn - yn + kM1;
