@@ -244,6 +244,11 @@ typedef struct {
     uint64_t batches, pending;    /* batches launched, requests waiting now         */
     uint64_t tiles;               /* work tiles launched                            */
     double worker_busy_s;         /* worker time spent planning and launching       */
+    uint64_t arena_used_bytes;    /* output bytes held now                          */
+    uint64_t arena_free_blocks;   /* free fragments of the output arena now         */
+    uint64_t arena_top_bytes;     /* highest output offset handed out so far        */
+    uint64_t flights_busy;        /* batches on the device now                      */
+    double gpu_busy_s;            /* summed device time of the finished batches     */
 } prand_server_stats_t;
 
 /* output_bytes: device arena for outputs (a request whose output does not fit

@@ -49,7 +49,9 @@ class PrandError(RuntimeError):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(nm, ctypes.c_uint64) for nm in ("completed", "samples", "hits", "misses", "spills", "restores",
-                                                 "batches", "pending", "tiles")] + [("worker_busy_s", ctypes.c_double)]
+                                                 "batches", "pending", "tiles")] + [("worker_busy_s", ctypes.c_double)] + \
+        [(nm, ctypes.c_uint64) for nm in ("arena_used_bytes", "arena_free_blocks", "arena_top_bytes", "flights_busy")] + \
+        [("gpu_busy_s", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):

@@ -204,12 +204,20 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
     __syncwarp();
 }
 
-// ------------------------------------------------------------------ the persistent kernel
-template <typename OutT>
+// ------------------------------------------------------------------ the persistent kernels
+// Two builds of the same loop: MT19937 tiles only (jump chains that need many
+// registers) and every other generator (far fewer registers, so about twice
+// the resident warps).  A batch's MT19937 tiles come first in its tile list.
+enum { kModeMt = 0, kModeRest = 1 };
+
+template <typename OutT, int MODE>
 __device__ __forceinline__ void batch_tile(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
 {
+    if constexpr (MODE == kModeMt) {
+        batch_mt<OutT>(T, C, wsm, lane);
+        return;
+    }
     switch (T.gen) {
-    case PRAND_MT19937: batch_mt<OutT>(T, C, wsm, lane); break;
     case PRAND_MRG32K3A: batch_mrg<OutT>(T, C, wsm, lane); break;
     case PRAND_LFSR113: batch_lfsr<OutT>(T, C, wsm, lane); break;
     case PRAND_GM19: batch_gm<PRAND_GM19, OutT>(T, C, wsm, lane); break;
@@ -223,7 +231,8 @@ __device__ __forceinline__ void batch_tile(const BatchTile &T, const BatchCtx &C
     }
 }
 
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
+template <int MODE>
+__global__ void __launch_bounds__(kBatchThreads, (MODE == 1 ? 20 : 1)) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
                                                               uint32_t *counter, BatchCtx ctx)
 {
     __shared__ __align__(16) unsigned char smem[kBatchThreads / 32][kWarpSmem];
@@ -235,18 +244,19 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchTile *_
         t = __shfl_sync(kFull, t, 0);
         if (t >= ntiles) return;
         const BatchTile T = tiles[t];
-        if (T.dtype == PRAND_DTYPE_U32) batch_tile<uint32_t>(T, ctx, wsm, lane);
-        else if (T.dtype == PRAND_DTYPE_F32) batch_tile<float>(T, ctx, wsm, lane);
-        else batch_tile<double>(T, ctx, wsm, lane);
+        if (T.dtype == PRAND_DTYPE_U32) batch_tile<uint32_t, MODE>(T, ctx, wsm, lane);
+        else if (T.dtype == PRAND_DTYPE_F32) batch_tile<float, MODE>(T, ctx, wsm, lane);
+        else batch_tile<double, MODE>(T, ctx, wsm, lane);
         __syncwarp();
         if (ctx.tiles_left && lane == 0) {
             // the request's last tile to finish publishes its completion: every
-            // tile fences its writes before counting down, the last one fences
-            // to system scope before the host-visible flag
+            // tile fences its writes before counting down; the last one fences
+            // to system scope and appends the request to the host-visible list
             __threadfence();
             if (atomicSub(&ctx.tiles_left[T.req], 1u) == 1u) {
                 __threadfence_system();
-                ctx.req_done[T.req] = 1u;
+                const uint32_t slot = atomicAdd(ctx.done_count, 1u);
+                ctx.done_list[slot] = T.req + 1u;
             }
         }
         __syncwarp();
@@ -275,7 +285,10 @@ struct Engine {
     cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
     uint32_t *d_counter = nullptr;
     BatchParams params;
-    int sms = 152, blocks_per_sm = 1;
+    int sms = 152, blocks_per_sm[2] = { 1, 1 };  // per kernel build
+    cudaStream_t aux = nullptr;                   // second branch of mixed launches
+    cudaEvent_t fork = nullptr, join = nullptr;
+    std::mutex aux_mu;
     bool ready = false;
 };
 
@@ -295,10 +308,17 @@ prand_status_t engine_get(Engine **out)
         if (cudaMalloc(&E.d_counter, 64) != cudaSuccess) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
         cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev);
-        int bps = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel, kBatchThreads, 0) != cudaSuccess || bps < 1)
-            bps = 1;
-        E.blocks_per_sm = bps;
+        for (int m = 0; m < 2; ++m) {
+            int bps = 0;
+            const cudaError_t e = m == kModeMt
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeMt>, kBatchThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeRest>, kBatchThreads, 0);
+            E.blocks_per_sm[m] = (e == cudaSuccess && bps >= 1) ? bps : 1;
+        }
+        if (cudaStreamCreateWithFlags(&E.aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&E.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&E.join, cudaEventDisableTiming) != cudaSuccess)
+            return PRAND_ERR_CUDA;
         const char *path = getenv("PRAND_TUNE_CACHE");
         if (path) {
             FILE *f = fopen(path, "r");
@@ -362,7 +382,7 @@ prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTable
     if ((s = engine_bases(*E, seed, st, &B)) != PRAND_OK) return s;
     memset(ctx, 0, sizeof *ctx);
     ctx->mrg_tab = E->T->mrg;
-    ctx->lfsr_tab = E->T->lfsr4;
+    ctx->lfsr_tab = E->T->lfsr;
     ctx->mt_polys = E->T->mt;
     for (int g = 0; g < 8; ++g) ctx->gm_tab[g] = E->T->gm[g];
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) ctx->base[g] = (const char *)B->dev + B->off[g];
@@ -467,25 +487,49 @@ prand_status_t validate_requests(const prand_request_t *reqs, size_t n)
     return PRAND_OK;
 }
 
-unsigned batch_grid(uint32_t ntiles)
+static unsigned batch_grid(uint32_t ntiles, int mode)
 {
     Engine *E;
     if (engine_get(&E) != PRAND_OK) return 1;
     uint64_t warps_needed = ntiles, per_block = kBatchThreads / 32;
-    uint64_t g = std::min<uint64_t>((warps_needed + per_block - 1) / per_block, (uint64_t)E->sms * E->blocks_per_sm);
+    uint64_t g = std::min<uint64_t>((warps_needed + per_block - 1) / per_block, (uint64_t)E->sms * E->blocks_per_sm[mode]);
     return (unsigned)std::max<uint64_t>(g, 1);
 }
 
-prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t *d_counter, const BatchCtx &ctx,
-                            cudaStream_t st)
+uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles)
 {
-    if (cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
+    uint32_t n = 0;
+    while (n < tiles.size() && tiles[n].gen == PRAND_MT19937) ++n;
+    return n;
+}
+
+// tiles [0, nmt) are MT19937 tiles (counter[0]), the rest any other generator
+// (counter[1]).  When both kinds are present the MT19937 part runs on `aux`,
+// forked from and joined back into `st` with the two events.
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t *d_counter,
+                            const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
+{
+    if (cudaMemsetAsync(d_counter, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
     if (!ntiles) return PRAND_OK;
-    batch_kernel<<<batch_grid(ntiles), kBatchThreads, 0, st>>>(d_tiles, ntiles, d_counter, ctx);
+    const uint32_t nrest = ntiles - nmt;
+    prand_status_t s = PRAND_OK;
+    if (nmt && nrest) {
+        if (!aux || cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
+            return PRAND_ERR_CUDA;
+        batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, aux>>>(d_tiles, nmt, d_counter, ctx);
+        if ((s = launch_check()) != PRAND_OK) return s;
+        batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles + nmt, nrest,
+                                                                                        d_counter + 1, ctx);
+        if ((s = launch_check()) != PRAND_OK) return s;
+        if (cudaEventRecord(join, aux) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+            return PRAND_ERR_CUDA;
+        return PRAND_OK;
+    }
+    if (nmt) batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, st>>>(d_tiles, nmt, d_counter, ctx);
+    else batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles, nrest, d_counter + 1, ctx);
     return launch_check();
 }
 
-// Tiles to the device through the engine's pinned staging buffer.
 prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter)
 {
     Engine *E;
@@ -523,7 +567,9 @@ using namespace prand;
 struct prand_batch_plan_s {
     int device = -1;
     BatchTile *d_tiles = nullptr;
-    uint32_t ntiles = 0;
+    uint32_t ntiles = 0, nmt = 0;
+    cudaStream_t aux = nullptr;  // the second branch while capturing
+    cudaEvent_t fork = nullptr, join = nullptr;
     uint32_t *d_counter = nullptr;
     BatchCtx ctx;
     cudaGraph_t graph = nullptr;
@@ -548,7 +594,11 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
     BatchTile *d_tiles;
     uint32_t *counter;
     if ((s = upload_tiles(tiles, st, &d_tiles, &counter)) != PRAND_OK) return s;
-    return launch_batch(d_tiles, (uint32_t)tiles.size(), counter, ctx, st);
+    Engine *E;
+    if ((s = engine_get(&E)) != PRAND_OK) return s;
+    std::lock_guard<std::mutex> lk(E->aux_mu);  // one user of the second branch at a time
+    return launch_batch(d_tiles, (uint32_t)tiles.size(), count_mt_tiles(tiles), counter, ctx, st, E->aux, E->fork,
+                        E->join);
 }
 
 prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_request_t *reqs, size_t n, uint64_t seed)
@@ -563,6 +613,9 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     cudaStream_t cap = nullptr;
     auto fail = [&](prand_status_t e) {
         if (cap) cudaStreamDestroy(cap);
+        if (p->aux) cudaStreamDestroy(p->aux);
+        if (p->fork) cudaEventDestroy(p->fork);
+        if (p->join) cudaEventDestroy(p->join);
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);
         if (p->d_tiles) cudaFree(p->d_tiles);
@@ -577,17 +630,23 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     order_tiles(tiles);
     if (tiles.size() > 0xFFFFFFFFull) return fail(PRAND_ERR_ARG);
     p->ntiles = (uint32_t)tiles.size();
+    p->nmt = count_mt_tiles(tiles);
     if (cudaMalloc(&p->d_counter, 64) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(PRAND_ERR_CUDA);
     if (p->ntiles) {
         if (cudaMalloc(&p->d_tiles, tiles.size() * sizeof(BatchTile)) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
         if (cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(PRAND_ERR_CUDA);
     }
     if (cudaStreamSynchronize(0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-    // capture: counter reset + the persistent launch
+    // capture: counter reset + the persistent launches (the MT19937 branch forked
+    // onto the plan's second stream and joined back)
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->d_counter, p->ctx, cap);
+    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->nmt, p->d_counter, p->ctx, cap, p->aux, p->fork, p->join);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     p->graph = g;
@@ -616,6 +675,9 @@ prand_status_t prand_batch_plan_destroy(prand_batch_plan_t p)
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->d_counter) cudaFree(p->d_counter);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
     delete p;
     return PRAND_OK;
 }

@@ -34,7 +34,8 @@ struct BatchCtx {
     const void *base[PRAND_NUM_GENERATORS];  // base states of the batch's seed
     void *slots[PRAND_NUM_GENERATORS];       // resident-state arenas (server)
     uint32_t *tiles_left;                    // per request: tiles not finished (server), or null
-    volatile uint32_t *req_done;             // per request: set to 1 in mapped host memory when done
+    volatile uint32_t *done_list;            // mapped host memory: request index + 1, in completion order
+    uint32_t *done_count;                    // device counter of done_list entries (zero at launch)
 };
 
 struct BatchParams {
@@ -52,7 +53,12 @@ size_t slot_words(int gen);  // 32-bit words per state slot
 prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter);
 void order_tiles(std::vector<BatchTile> &tiles);
 prand_status_t validate_requests(const prand_request_t *reqs, size_t n);
-prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t *d_counter, const BatchCtx &ctx,
-                            cudaStream_t st);
+// Tiles [0, nmt) are MT19937 tiles, the rest other generators (order_tiles
+// puts MT19937 first).  Mixed lists run the MT19937 part on `aux`, forked from
+// and joined into `st` with the two events; a list of one kind needs none.
+uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles);
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t *d_counter,
+                            const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux = nullptr,
+                            cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 }  // namespace prand

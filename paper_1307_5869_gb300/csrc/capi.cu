@@ -50,7 +50,7 @@ prand_status_t get_tables(int gen, DevTables **out)
     T.device = dev;
     if (!T.ready_basic) {
         size_t mrg_b = (size_t)kJumpBits * 18 * sizeof(uint32_t);
-        size_t lfsr_b = (size_t)4 * kJumpBits * (32 + 128) * sizeof(uint32_t);  // column + nibble tables
+        size_t lfsr_b = (size_t)4 * kJumpBits * 32 * sizeof(uint32_t);
         size_t gm_b = (size_t)kJumpBits * 4 * sizeof(uint64_t);
         if (cudaMalloc(&T.mrg, mrg_b) != cudaSuccess) return PRAND_ERR_NOMEM;
         if (cudaMalloc(&T.lfsr, lfsr_b) != cudaSuccess) return PRAND_ERR_NOMEM;
@@ -58,7 +58,6 @@ prand_status_t get_tables(int gen, DevTables **out)
             if (cudaMalloc(&T.gm[g], gm_b) != cudaSuccess) return PRAND_ERR_NOMEM;
         prand_status_t s = mrg_build_table(T.mrg, 0);
         if (s == PRAND_OK) s = lfsr_build_table(T.lfsr, 0);
-        T.lfsr4 = T.lfsr + (size_t)4 * kJumpBits * 32;
         for (int g = 0; g < 8 && s == PRAND_OK; ++g) s = gm_build_table(PRAND_GM19 + g, T.gm[g], 0);
         if (s == PRAND_OK && cudaDeviceSynchronize() != cudaSuccess) s = PRAND_ERR_CUDA;
         if (s != PRAND_OK) return s;

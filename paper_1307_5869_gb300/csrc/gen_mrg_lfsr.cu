@@ -150,19 +150,6 @@ __global__ void lfsr_table_kernel(uint32_t *tab)
     }
 }
 
-// Nibble tables from the column tables: one thread per entry.
-__global__ void lfsr_table4_kernel(const uint32_t *tab, uint32_t *tab4)
-{
-    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= 4u * kJumpBits * 128u) return;
-    const uint32_t v = id & 15u, k = (id >> 4) & 7u, cb = id >> 7;  // cb = c * kJumpBits + b
-    const uint32_t *col = tab + (size_t)cb * 32;
-    uint32_t r = 0;
-    for (int i = 0; i < 4; ++i)
-        if ((v >> i) & 1u) r ^= col[4 * k + i];
-    tab4[id] = r;
-}
-
 // Default state: 987654321 in all four words (L'Ecuyer's example seed; the paper
 // prints none).  Seeded: the high 32 bits of SplitMix64 draws, redrawn while
 // the top p bits of a component are all zero.
@@ -271,14 +258,9 @@ prand_status_t mrg_build_table(uint32_t *tab, cudaStream_t st)
     return launch_check();
 }
 
-// tab: [4][kJumpBits][32] column images, then tab4 = tab + 4 * kJumpBits * 32:
-// [4][kJumpBits][8][16] nibble tables (the form the jumps use).
 prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st)
 {
     lfsr_table_kernel<<<1, 32, 0, st>>>(tab);
-    prand_status_t s = launch_check();
-    if (s != PRAND_OK) return s;
-    lfsr_table4_kernel<<<(4 * kJumpBits * 128 + 255) / 256, 256, 0, st>>>(tab, tab + 4 * kJumpBits * 32);
     return launch_check();
 }
 
@@ -296,7 +278,7 @@ prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, vo
     if (gen == PRAND_MRG32K3A)
         mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
     else
-        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr4, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
     return launch_check();
 }
 
@@ -304,7 +286,7 @@ prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_
 {
     const unsigned B = 128;
     if (gen == PRAND_MRG32K3A) mrg_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (uint32_t *)d_state, n, off);
-    else lfsr_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr4, (uint32_t *)d_state, n, off);
+    else lfsr_skip_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (uint32_t *)d_state, n, off);
     return launch_check();
 }
 
@@ -347,8 +329,8 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
         if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
         else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     } else {
-        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr4, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
-        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr4, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     }
     return launch_check();
 }

@@ -128,22 +128,11 @@ __device__ __forceinline__ uint32_t gf2_apply(const uint32_t *col, uint32_t v)
     return r;
 }
 
-// The same maps as nibble tables: t4[k * 16 + v] = image of the word whose
-// only set bits are v in nibble k (the XOR of four column images), so one
-// application is eight table reads instead of 32 conditional XORs.
-// tab4[((c * kJumpBits + b) * 8 + k) * 16 + v] for component c, power 2^b.
-__device__ __forceinline__ uint32_t gf2_apply4(const uint32_t *t4, uint32_t v)
+// The lookups depend only on the bit b, so every lane of a warp reads the same
+// 32 words: one broadcast per word, whatever the lanes' states.
+__device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint32_t z[4])
 {
-    uint32_t r = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) r ^= t4[16 * k + ((v >> (4 * k)) & 15u)];
-    return r;
-}
-
-__device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab4, int b, uint32_t z[4])
-{
-#pragma unroll
-    for (int c = 0; c < 4; ++c) z[c] = gf2_apply4(tab4 + ((size_t)c * kJumpBits + b) * 128, z[c]);
+    for (int c = 0; c < 4; ++c) z[c] = gf2_apply(tab + ((size_t)c * kJumpBits + b) * 32, z[c]);
 }
 
 __device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)

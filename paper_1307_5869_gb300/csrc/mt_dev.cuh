@@ -80,15 +80,16 @@ __device__ __forceinline__ void mt_twist_emit(const uint32_t *__restrict__ ob, u
 }
 
 // Twist of one block out of place (no output): the 20-chunk in-order schedule
-// of mt_twist_emit_chunks.
+// of mt_twist_emit_chunks, kept as a compact loop (it runs inside the jump's
+// unrolled sliding-window loop, where code size matters more than its cost).
 __device__ __forceinline__ void mt_twist_block(const uint32_t *ob, uint32_t *nb, int lane)
 {
-#pragma unroll
+#pragma unroll 4
     for (int c = 0; c < 20; ++c) {
         const int k = 32 * c + lane;
-        if (c < 19 || lane < kMtN - 32 * 19) {
-            const uint32_t b = (c < 19 || lane < kMtN - 32 * 19 - 1) ? ob[k + 1] : nb[0];
-            const uint32_t p = c < 7 ? ob[k + 397] : c > 7 ? nb[k - 227] : (lane < 3 ? ob[k + 397] : nb[k - 227]);
+        if (k < kMtN) {
+            const uint32_t b = k + 1 < kMtN ? ob[k + 1] : nb[0];
+            const uint32_t p = k < 227 ? ob[k + 397] : nb[k - 227];
             nb[k] = mt_recur(ob[k], b, p);
         }
         if ((c & 3) == 3) __syncwarp();

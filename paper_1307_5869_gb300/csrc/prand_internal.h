@@ -63,7 +63,6 @@ struct DevTables {
     int device = -1;
     uint32_t *mrg = nullptr;      // [kJumpBits][18]: A^(2^b) mod m1 (9 words), B^(2^b) mod m2 (9 words)
     uint32_t *lfsr = nullptr;     // [4][kJumpBits][32]: column images of T_c^(2^b)
-    uint32_t *lfsr4 = nullptr;    // [4][kJumpBits][8][16]: the same maps as nibble tables (jumps use these)
     uint64_t *gm[8] = {};         // per GM/GQ generator: [kJumpBits][4] = M^(2^b) mod p
     uint32_t *mt = nullptr;       // [kMtPolyCount][kMtPolyWords]: x^(2^b) mod phi
     bool ready_basic = false;

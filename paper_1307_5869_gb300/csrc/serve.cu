@@ -44,6 +44,7 @@ size_t esz(int dtype) { return dtype == PRAND_DTYPE_F64 ? 8 : 4; }
 // First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
 struct Arena {
     std::map<uint64_t, uint64_t> free_;  // offset -> bytes
+    uint64_t used = 0, top = 0;
     explicit Arena(uint64_t cap = 0) { if (cap) free_[0] = cap; }
     bool alloc(uint64_t bytes, uint64_t *off)
     {
@@ -54,6 +55,8 @@ struct Arena {
                 const uint64_t rest = it->second - bytes, roff = it->first + bytes;
                 free_.erase(it);
                 if (rest) free_[roff] = rest;
+                used += bytes;
+                top = std::max(top, roff);
                 return true;
             }
         return false;
@@ -61,6 +64,7 @@ struct Arena {
     void release(uint64_t off, uint64_t bytes)
     {
         bytes = (bytes + 255) & ~255ull;
+        used -= bytes;
         auto it = free_.emplace(off, bytes).first;
         auto nx = std::next(it);
         if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
@@ -113,11 +117,12 @@ struct FlightReq {
 
 struct Flight {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, ev0 = nullptr;  // end and start of the batch on the device
     BatchTile *h_tiles = nullptr, *d_tiles = nullptr;  // kFlightTiles each
     uint32_t *counter = nullptr;
     uint32_t *h_left = nullptr, *d_left = nullptr;  // tiles per request (staging, device countdown)
-    volatile uint32_t *h_done = nullptr;            // per-request completion flags (mapped host memory)
+    volatile uint32_t *h_done = nullptr;            // completed request indices + 1, in completion order (mapped host memory)
+    size_t cursor = 0;                              // next h_done entry to read
     std::vector<FlightReq> reqs;
     std::vector<std::vector<uint32_t>> restored;    // host copies of restored states, kept until the batch ends
     size_t ndone = 0;
@@ -149,7 +154,7 @@ struct prand_server_s {
     std::deque<uint64_t> pending[2];
     std::unordered_map<uint64_t, SReq> reqs;
     uint64_t next_id = 1;
-    uint32_t max_batch_reqs[2] = { 2048, 128 };
+    uint32_t max_batch_reqs[2] = { 512, 64 };
     Flight fl[kFlights];
     std::thread worker;
     std::mutex mu;
@@ -218,13 +223,20 @@ void complete_flights(prand_server_s *S)
     for (Flight &F : S->fl) {
         if (!F.busy) continue;
         const double t = now_s();
-        for (size_t i = 0; i < F.reqs.size() && F.ndone < F.reqs.size(); ++i) {
-            FlightReq &q = F.reqs[i];
-            if (!q.done && F.h_done[i]) { finish_request(S, q, t); ++F.ndone; }
+        // new entries of the device's completion list (a slot may be filled out
+        // of order; reading stops at the first one not yet written)
+        while (F.cursor < F.reqs.size()) {
+            const uint32_t v = F.h_done[F.cursor];
+            if (v == 0 || v > F.reqs.size()) break;
+            FlightReq &q = F.reqs[v - 1];
+            if (!q.done) { finish_request(S, q, t); ++F.ndone; }
+            ++F.cursor;
         }
         cudaError_t e = cudaEventQuery(F.ev);
         if (e == cudaErrorNotReady) continue;
         if (e != cudaSuccess) S->error = PRAND_ERR_CUDA;
+        float ms = 0;
+        if (e == cudaSuccess && cudaEventElapsedTime(&ms, F.ev0, F.ev) == cudaSuccess) S->stats.gpu_busy_s += 1e-3 * ms;
         for (FlightReq &q : F.reqs)
             if (!q.done) finish_request(S, q, t);
         F.reqs.clear();
@@ -325,6 +337,7 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
         memset(F.h_left, 0, nr * 4);
         for (const BatchTile &t : tiles) F.h_left[t.req]++;
         for (size_t i = 0; i < nr; ++i) F.h_done[i] = 0;
+        F.cursor = 0;
     }
     if (lane == 1) order_tiles(tiles);  // the fast lane's tiles are alike: no sort
     const size_t n = tiles.size();
@@ -332,10 +345,13 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
         memcpy(F.h_tiles, tiles.data(), n * sizeof(BatchTile));
         BatchCtx ctx = S->ctx;
         ctx.tiles_left = F.d_left;
-        ctx.req_done = F.h_done;
-        if (cudaMemcpyAsync(F.d_tiles, F.h_tiles, n * sizeof(BatchTile), cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
+        ctx.done_list = F.h_done;
+        ctx.done_count = F.counter + 4;  // its own 16-byte slot of the flight's counter block
+        if (cudaEventRecord(F.ev0, F.st) != cudaSuccess ||
+            cudaMemsetAsync(F.counter + 4, 0, sizeof(uint32_t), F.st) != cudaSuccess ||
+            cudaMemcpyAsync(F.d_tiles, F.h_tiles, n * sizeof(BatchTile), cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
             cudaMemcpyAsync(F.d_left, F.h_left, nr * 4, cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
-            launch_batch(F.d_tiles, (uint32_t)n, F.counter, ctx, F.st) != PRAND_OK ||
+            launch_batch(F.d_tiles, (uint32_t)n, count_mt_tiles(tiles), F.counter, ctx, F.st) != PRAND_OK ||
             cudaEventRecord(F.ev, F.st) != cudaSuccess)
             S->error = PRAND_ERR_CUDA;
     }
@@ -344,6 +360,28 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
     S->stats.batches++;
     S->stats.tiles += n;
     return true;
+}
+
+// Queue one request (the server lock held).
+prand_status_t submit_locked(prand_server_s *S, int32_t gen, uint64_t stream, uint64_t length, int32_t dtype,
+                             uint64_t *id)
+{
+    if (gen < 0 || gen >= PRAND_NUM_GENERATORS || dtype < 0 || dtype > 2 || length == 0) return PRAND_ERR_ARG;
+    uint64_t bytes;
+    if (__builtin_mul_overflow(length, (uint64_t)esz(dtype), &bytes) || ((bytes + 255) & ~255ull) > S->out_cap)
+        return PRAND_ERR_ARG;  // can never fit the output arena
+    if (S->error != PRAND_OK) return S->error;
+    SReq r;
+    r.gen = gen;
+    r.dtype = dtype;
+    r.stream = stream;
+    r.len = length;
+    r.bytes = bytes;
+    r.t_arr = now_s();
+    *id = S->next_id++;
+    S->reqs[*id] = r;
+    S->pending[gen == PRAND_MT19937 ? 1 : 0].push_back(*id);
+    return PRAND_OK;
 }
 
 void worker_loop(prand_server_s *S)
@@ -384,6 +422,7 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
     auto fail = [&](prand_status_t e) {
         for (Flight &F : S->fl) {
             if (F.ev) cudaEventDestroy(F.ev);
+            if (F.ev0) cudaEventDestroy(F.ev0);
             if (F.st) cudaStreamDestroy(F.st);
             if (F.counter) cudaFree(F.counter);
             if (F.d_tiles) cudaFree(F.d_tiles);
@@ -416,7 +455,7 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
     }
     for (Flight &F : S->fl) {
         if (cudaStreamCreateWithFlags(&F.st, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-        if (cudaEventCreateWithFlags(&F.ev, cudaEventDisableTiming) != cudaSuccess) return fail(PRAND_ERR_CUDA);
+        if (cudaEventCreate(&F.ev) != cudaSuccess || cudaEventCreate(&F.ev0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
         if (cudaMalloc(&F.counter, 64) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
         void *hd = nullptr;
         if (cudaMallocHost(&F.h_tiles, kFlightTiles * sizeof(BatchTile)) != cudaSuccess ||
@@ -436,24 +475,11 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
 prand_status_t prand_server_submit(prand_server_t S, int32_t gen, uint64_t stream, uint64_t length, int32_t dtype,
                                    uint64_t *id)
 {
-    if (!S || !id || gen < 0 || gen >= PRAND_NUM_GENERATORS || dtype < 0 || dtype > 2 || length == 0) return PRAND_ERR_ARG;
-    uint64_t bytes;
-    if (__builtin_mul_overflow(length, (uint64_t)esz(dtype), &bytes) || ((bytes + 255) & ~255ull) > S->out_cap)
-        return PRAND_ERR_ARG;  // can never fit the output arena
+    if (!S || !id) return PRAND_ERR_ARG;
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->error != PRAND_OK) return S->error;
-    SReq r;
-    r.gen = gen;
-    r.dtype = dtype;
-    r.stream = stream;
-    r.len = length;
-    r.bytes = bytes;
-    r.t_arr = now_s();
-    *id = S->next_id++;
-    S->reqs[*id] = r;
-    S->pending[gen == PRAND_MT19937 ? 1 : 0].push_back(*id);
-    S->cv.notify_one();
-    return PRAND_OK;
+    prand_status_t s = submit_locked(S, gen, stream, length, dtype, id);
+    if (s == PRAND_OK) S->cv.notify_one();
+    return s;
 }
 
 prand_status_t prand_server_query(prand_server_t S, uint64_t id, int32_t *done, void **dev_out, double *latency_s)
@@ -506,6 +532,11 @@ prand_status_t prand_server_stats(prand_server_t S, prand_server_stats_t *out)
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->stats;
     out->pending = S->pending[0].size() + S->pending[1].size();
+    out->arena_used_bytes = S->arena.used;
+    out->arena_free_blocks = S->arena.free_.size();
+    out->arena_top_bytes = S->arena.top;
+    out->flights_busy = 0;
+    for (const Flight &F : S->fl) out->flights_busy += F.busy;
     return S->error;
 }
 
@@ -522,6 +553,7 @@ prand_status_t prand_server_destroy(prand_server_t S)
     for (Flight &F : S->fl) {
         if (F.st) cudaStreamSynchronize(F.st);
         if (F.ev) cudaEventDestroy(F.ev);
+        if (F.ev0) cudaEventDestroy(F.ev0);
         if (F.st) cudaStreamDestroy(F.st);
         if (F.counter) cudaFree(F.counter);
         if (F.d_tiles) cudaFree(F.d_tiles);
@@ -564,29 +596,44 @@ prand_status_t prand_server_replay(prand_server_t S, const prand_request_t *reqs
     }
     std::unordered_map<uint64_t, size_t> index;
     index.reserve(2 * n);
-    std::vector<uint64_t> got(4096);
+    std::vector<std::pair<uint64_t, double>> fin;
     const double t0 = now_s();
     size_t next = 0, done = 0;
     prand_status_t err = PRAND_OK;
     while (done < n && err == PRAND_OK) {
         const double t = now_s() - t0;
-        while (next < n && arrival_s[next] <= t) {
-            const prand_request_t &r = reqs[next];
-            uint64_t id;
-            err = prand_server_submit(S, r.gen, r.stream, r.length, r.dtype, &id);
-            if (err != PRAND_OK) break;
-            index[id] = next;
-            ++next;
+        // submit every request that has arrived, under one lock
+        if (next < n && arrival_s[next] <= t) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            while (next < n && arrival_s[next] <= t) {
+                const prand_request_t &r = reqs[next];
+                uint64_t id;
+                err = submit_locked(S, r.gen, r.stream, r.length, r.dtype, &id);
+                if (err != PRAND_OK) break;
+                index[id] = next;
+                ++next;
+            }
+            S->cv.notify_one();
         }
-        size_t k = 0;
-        if (err == PRAND_OK) err = prand_server_completed(S, got.data(), got.size(), &k);
-        for (size_t i = 0; i < k && err == PRAND_OK; ++i) {
-            double lat = 0;
-            int32_t d = 0;
-            err = prand_server_query(S, got[i], &d, nullptr, &lat);
-            auto it = index.find(got[i]);
-            if (it != index.end()) { latency_s[it->second] = lat; index.erase(it); ++done; }
-            prand_server_release(S, got[i]);
+        // collect and release every completed request under one lock
+        fin.clear();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->error != PRAND_OK) err = S->error;
+            for (uint64_t id : S->done_q) {
+                auto it = S->reqs.find(id);
+                if (it == S->reqs.end()) continue;
+                fin.emplace_back(id, it->second.t_done - it->second.t_arr);
+                S->arena.release(it->second.off, it->second.bytes);
+                S->reqs.erase(it);
+            }
+            S->done_q.clear();
+            if (!fin.empty()) S->cv.notify_one();
+        }
+        const size_t k = fin.size();
+        for (const auto &f : fin) {
+            auto it = index.find(f.first);
+            if (it != index.end()) { latency_s[it->second] = f.second; index.erase(it); ++done; }
         }
         if (k == 0 && next < n && arrival_s[next] > now_s() - t0 + 50e-6)
             std::this_thread::sleep_for(std::chrono::microseconds(20));
