@@ -157,11 +157,13 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
         idx = src[kMtN];
         __syncwarp();
     } else {
+        // stream k = base advanced by k 2^432: one polynomial per nonzero hex digit of k
         const uint32_t *src = (const uint32_t *)C.base[PRAND_MT19937];
         bool first = true;
-        for (int b = 0; b < 64; ++b) {
-            if (!((T.stream >> b) & 1u)) continue;
-            mt_apply_poly_warp(C.mt_polys + (size_t)(kMtStreamShift + b) * kMtPolyWords, first ? src : b0, b0, b0, lane);
+        for (int i = 0; i < kMtWinPositions; ++i) {
+            const uint32_t d = (uint32_t)(T.stream >> (4 * i)) & 15u;
+            if (!d) continue;
+            mt_apply_poly_warp(C.mt_win + ((size_t)i * 16 + d) * kMtPolyWords, first ? src : b0, b0, b0, lane);
             first = false;
             __syncwarp();
         }
@@ -384,6 +386,8 @@ prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTable
     ctx->mrg_tab = E->T->mrg;
     ctx->lfsr_tab = E->T->lfsr;
     ctx->mt_polys = E->T->mt;
+    if ((s = get_mt_window(E->T)) != PRAND_OK) return s;
+    ctx->mt_win = E->T->mt_win;
     for (int g = 0; g < 8; ++g) ctx->gm_tab[g] = E->T->gm[g];
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) ctx->base[g] = (const char *)B->dev + B->off[g];
     if (T) *T = E->T;

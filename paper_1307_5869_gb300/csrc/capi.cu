@@ -41,6 +41,19 @@ DevTables g_tables[kMaxDevices];
 std::mutex g_tables_mu;
 }  // namespace
 
+prand_status_t get_mt_window(DevTables *T)
+{
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if (T->ready_mt_win) return PRAND_OK;
+    const uint32_t *host = mt_host_window_polys();
+    if (!host) return PRAND_ERR_STATE;
+    const size_t bytes = (size_t)kMtWinPositions * 16 * kMtPolyWords * sizeof(uint32_t);
+    if (cudaMalloc(&T->mt_win, bytes) != cudaSuccess) return PRAND_ERR_NOMEM;
+    if (cudaMemcpy(T->mt_win, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
+    T->ready_mt_win = true;
+    return PRAND_OK;
+}
+
 prand_status_t get_tables(int gen, DevTables **out)
 {
     int dev = 0;

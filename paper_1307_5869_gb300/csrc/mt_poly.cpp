@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "prand_internal.h"
@@ -134,9 +135,35 @@ void square_into(const Poly &a, Poly &out)
     }
 }
 
+// a * b (degrees < kDeg, carry-less) into out, reduced mod phi.  For every set
+// bit of b, a copy of a shifted by that bit is added: the 64 shifts of a within
+// a word are made once, so each set bit costs one pass over a's words.
+void mul_into(const Poly &a, const Poly &b, Poly &out, const Reducer &red)
+{
+    const int nw = (kDeg + 63) / 64;  // words of a reduced polynomial
+    std::vector<Poly> sh(64, Poly((size_t)nw + 1, 0));
+    for (int s = 0; s < 64; ++s)
+        for (int w = 0; w <= nw; ++w) {
+            const uint64_t lo = w < nw ? a[(size_t)w] : 0, prev = w > 0 ? a[(size_t)(w - 1)] : 0;
+            sh[(size_t)s][(size_t)w] = s ? (lo << s) | (prev >> (64 - s)) : lo;
+        }
+    std::fill(out.begin(), out.end(), 0ull);
+    for (int w = 0; w < nw; ++w) {
+        uint64_t v = b[(size_t)w];
+        while (v) {
+            const int s = __builtin_ctzll(v);
+            v &= v - 1;
+            const Poly &A = sh[(size_t)s];
+            for (int k = 0; k <= nw; ++k) out[(size_t)(w + k)] ^= A[(size_t)k];
+        }
+    }
+    red.reduce(out);
+}
+
 std::vector<uint32_t> g_polys;
 std::once_flag g_once;
 bool g_ok = false;
+Poly g_phi;  // kept for the window table
 
 void compute()
 {
@@ -147,6 +174,7 @@ void compute()
     Poly phi((size_t)kW, 0);
     for (int j = 0; j <= L; ++j)
         if (getb(C, L - j)) flipb(phi, j);
+    g_phi = phi;
     Reducer red(phi);
     g_polys.assign((size_t)kMtPolyCount * kMtPolyWords, 0u);
     Poly cur((size_t)kW, 0), sq((size_t)kW, 0);
@@ -173,6 +201,56 @@ const uint32_t *mt_host_pow2_polys()
 {
     std::call_once(g_once, compute);
     return g_ok ? g_polys.data() : nullptr;
+}
+
+namespace {
+std::vector<uint32_t> g_win;
+std::once_flag g_win_once;
+bool g_win_ok = false;
+
+Poly from_words(const uint32_t *w)
+{
+    Poly p((size_t)kW, 0);
+    for (int k = 0; k < kMtPolyWords / 2; ++k) p[(size_t)k] = (uint64_t)w[2 * k] | ((uint64_t)w[2 * k + 1] << 32);
+    return p;
+}
+
+void compute_window()
+{
+    const uint32_t *pw = mt_host_pow2_polys();
+    if (!pw) return;
+    g_win.assign((size_t)kMtWinPositions * 16 * kMtPolyWords, 0u);
+    const Reducer red(g_phi);
+    // position i: x^(d 2^(kMtStreamShift + 4 i)) mod phi for digits d = 1..15;
+    // the powers of two are stored already, the other digits are one product each
+    auto position = [&](int i) {
+        std::vector<Poly> P(16);
+        for (int t = 0; t < 4; ++t) P[(size_t)(1 << t)] = from_words(pw + (size_t)(kMtStreamShift + 4 * i + t) * kMtPolyWords);
+        for (int d = 3; d < 16; ++d) {
+            if ((d & (d - 1)) == 0) continue;
+            const int hi = 1 << (31 - __builtin_clz((unsigned)d));
+            P[(size_t)d].assign((size_t)kW, 0);
+            mul_into(P[(size_t)hi], P[(size_t)(d - hi)], P[(size_t)d], red);
+        }
+        for (int d = 1; d < 16; ++d) {
+            uint32_t *dst = g_win.data() + ((size_t)i * 16 + d) * kMtPolyWords;
+            for (int k = 0; k < kMtPolyWords / 2; ++k) {
+                dst[2 * k] = (uint32_t)P[(size_t)d][(size_t)k];
+                dst[2 * k + 1] = (uint32_t)(P[(size_t)d][(size_t)k] >> 32);
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int i = 0; i < kMtWinPositions; ++i) th.emplace_back(position, i);
+    for (std::thread &t : th) t.join();
+    g_win_ok = true;
+}
+}  // namespace
+
+const uint32_t *mt_host_window_polys()
+{
+    std::call_once(g_win_once, compute_window);
+    return g_win_ok ? g_win.data() : nullptr;
 }
 
 }  // namespace prand
