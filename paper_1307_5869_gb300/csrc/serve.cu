@@ -101,6 +101,7 @@ struct Resident {
 };
 
 constexpr int kFlights = 32;
+constexpr int kMtFlights = 16;  // at most this many flights carry MT19937 batches
 // Fixed per-flight capacities, allocated once: growing a buffer in the loop
 // would free the old one, and cudaFree / cudaFreeHost wait for the whole
 // device, i.e. for every batch in flight.
@@ -396,7 +397,7 @@ void worker_loop(prand_server_s *S)
         const double tb = now_s();
         for (int lane = 0; lane < 2 && !launched; ++lane) {
             if (S->pending[lane].empty()) continue;
-            if (lane == 1 && mt_busy >= kFlights / 2) continue;  // the fast lane keeps half the flights
+            if (lane == 1 && mt_busy >= kMtFlights) continue;  // the rest of the flights stay with the fast lane
             for (Flight &F : S->fl)
                 if (!F.busy) { F.lane = lane; launched = launch_one(S, F, lane); break; }
         }
