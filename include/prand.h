@@ -134,6 +134,25 @@ prand_status_t prand_generate_host_u32(prand_handle_t h, uint32_t *host_out, uin
 prand_status_t prand_generate_host_f32(prand_handle_t h, float *host_out, uint64_t n_per_stream, prand_stream_t stream);
 prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint64_t n_per_stream, prand_stream_t stream);
 
+/* The streams as single-stream states for user code (prand_device.h, the
+ * paper's single-threaded interface, Sec. 7.4): prand_export_states writes
+ * one struct per stream, stream j at index j (prand_mt19937_state,
+ * prand_mrg32k3a_state, prand_lfsr113_state or prand_gm_state, of
+ * prand_device_state_bytes(gen) bytes each), at the streams' current
+ * positions; prand_import_states reads them back, so the handle continues from
+ * wherever user code left each stream.  dev_states: caller-owned device memory
+ * of n_streams structs, 8-byte aligned for GM/GQ and 4-byte aligned otherwise.
+ * MT19937 handles keep one in-block index for all streams: an import whose
+ * structs disagree on it returns PRAND_ERR_STATE and changes nothing (this
+ * check waits for `stream`).  The output position of prand_query is not
+ * changed by an import.  Asynchronous on `stream` otherwise.
+ * prand_device_state_bytes returns 0 for an unknown generator.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_STATE, PRAND_ERR_NOMEM,
+ * PRAND_ERR_CUDA. */
+uint64_t prand_device_state_bytes(prand_gen_t gen);
+prand_status_t prand_export_states(prand_handle_t h, void *dev_states, prand_stream_t stream);
+prand_status_t prand_import_states(prand_handle_t h, const void *dev_states, prand_stream_t stream);
+
 /* Advance every stream of the handle by the 256-bit offset offset_le[0] +
  * 2^64 offset_le[1] + 2^128 offset_le[2] + 2^192 offset_le[3] outputs
  * (rng_skipahead_, Sec. 7.2; jump methods of Sec. 5.1-5.4).

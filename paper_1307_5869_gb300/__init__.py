@@ -38,7 +38,8 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_mrg32k3a_generate_u32_noalloc", "prand_server_create", "prand_server_submit",
            "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
            "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
-           "prand_generate_host_f32", "prand_generate_host_f64"]
+           "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
+           "prand_import_states"]
 
 
 class PrandError(RuntimeError):
@@ -92,6 +93,10 @@ def load(build_if_missing: bool = False):
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
     L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
     L.prand_convert.argtypes = [ctypes.c_void_p, u64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    L.prand_device_state_bytes.argtypes = [ctypes.c_int]
+    L.prand_device_state_bytes.restype = u64
+    L.prand_export_states.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
+    L.prand_import_states.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
     vp = ctypes.c_void_p
     L.prand_server_create.argtypes = [ctypes.POINTER(vp), u64, u64, ctypes.c_uint32]
     L.prand_server_submit.argtypes = [vp, ctypes.c_int32, u64, u64, ctypes.c_int32, ctypes.POINTER(u64)]
@@ -112,7 +117,7 @@ def load(build_if_missing: bool = False):
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_float)]
     for nm in EXPORTS:
-        if nm not in ("prand_status_string", "prand_kernel_launches"):
+        if nm not in ("prand_status_string", "prand_kernel_launches", "prand_device_state_bytes"):
             getattr(L, nm).restype = ctypes.c_int
     _lib = L
     return L
@@ -169,6 +174,18 @@ def prand_generate_host_f32(h: int, host_out: int, n_per_stream: int, stream: in
 
 def prand_generate_host_f64(h: int, host_out: int, n_per_stream: int, stream: int = 0) -> None:
     _check(load().prand_generate_host_f64(h, host_out, n_per_stream, stream), "prand_generate_host_f64")
+
+
+def prand_device_state_bytes(gen) -> int:
+    return int(load().prand_device_state_bytes(_gid(gen)))
+
+
+def prand_export_states(h: int, dev_states: int, stream: int = 0) -> None:
+    _check(load().prand_export_states(h, dev_states, stream), "prand_export_states")
+
+
+def prand_import_states(h: int, dev_states: int, stream: int = 0) -> None:
+    _check(load().prand_import_states(h, dev_states, stream), "prand_import_states")
 
 
 def prand_skipahead(h: int, offset: int) -> None:

@@ -376,6 +376,35 @@ prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint6
     return generate_host(h, host_out, PRAND_DTYPE_F64, n_per_stream, stream);
 }
 
+uint64_t prand_device_state_bytes(prand_gen_t gen)
+{
+    return (gen < 0 || gen >= PRAND_NUM_GENERATORS) ? 0 : device_state_bytes((int)gen);
+}
+
+prand_status_t prand_export_states(prand_handle_t h, void *dev_states, prand_stream_t stream)
+{
+    if (!h || !dev_states) return PRAND_ERR_ARG;
+    if ((uintptr_t)dev_states % (is_gm(h->gen) ? 8 : 4)) return PRAND_ERR_ALIGN;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    s = export_states_dev(h->gen, h->d_state, h->n, h->mt_idx, dev_states, (cudaStream_t)stream);
+    if (s == PRAND_OK) h->last_stream = (cudaStream_t)stream;
+    return s;
+}
+
+prand_status_t prand_import_states(prand_handle_t h, const void *dev_states, prand_stream_t stream)
+{
+    if (!h || !dev_states) return PRAND_ERR_ARG;
+    if ((uintptr_t)dev_states % (is_gm(h->gen) ? 8 : 4)) return PRAND_ERR_ALIGN;
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    s = import_states_dev(h->gen, dev_states, h->n, h->d_state, &h->mt_idx, (cudaStream_t)stream);
+    if (s == PRAND_OK) h->last_stream = (cudaStream_t)stream;
+    return s;
+}
+
 prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4])
 {
     if (!h || !offset_le) return PRAND_ERR_ARG;

@@ -163,6 +163,14 @@ prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *
 // offset); *idx, the position inside the block shared by all streams, advances.
 prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);
 
+// States in the prand_device.h layout (states.cu): bytes per stream (0 for an
+// unknown generator), and the copies out of / into a handle's state arrays
+// (the import of MT19937 states checks that all share one block index and
+// waits for `st`).
+uint64_t device_state_bytes(int gen);
+prand_status_t export_states_dev(int gen, const void *d_state, uint64_t n, uint32_t mt_idx, void *out, cudaStream_t st);
+prand_status_t import_states_dev(int gen, const void *in, uint64_t n, void *d_state, uint32_t *mt_idx, cudaStream_t st);
+
 // Family-specific device work, all asynchronous on `st` unless noted.
 // Base state of one "stream" in the family's device layout.
 prand_status_t seed_base(int gen, uint64_t seed, void *d_base, cudaStream_t st);

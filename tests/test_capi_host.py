@@ -68,6 +68,10 @@ def test_argument_errors_without_device(lib):
     assert L.prand_convert(None, 0, 1, None, None) == 0           # nothing to do
     assert L.prand_convert(vp(0x1002), 4, 1, vp(0x2000), None) == 2  # input not 4-byte aligned
     assert L.prand_convert(vp(0x1000), 4, 2, vp(0x2004), None) == 2  # doubles not 8-byte aligned
+    assert L.prand_export_states(None, vp(0x1000), None) == 1
+    assert L.prand_import_states(None, vp(0x1000), None) == 1
+    assert [L.prand_device_state_bytes(g) for g in range(11)] == [2500, 24, 16] + [512] * 8
+    assert L.prand_device_state_bytes(11) == 0
 
 
 def test_binding_raises_on_error(lib):
