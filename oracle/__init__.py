@@ -58,6 +58,10 @@ def lib():
             L.orc_block_length.argtypes = [ctypes.c_int, u64p]
             L.orc_stream.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, vp]
             L.orc_stream_range.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, vp]
+            L.orc_stream_v.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64, vp]
+            L.orc_stream_range_v.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                             ctypes.c_uint64, vp]
+            L.orc_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), u64p]
             for nm in ("orc_gen_u32", "orc_gen_f32", "orc_gen_f64"):
                 getattr(L, nm).argtypes = [ctypes.c_int, vp, vp, ctypes.c_uint64]
             for nm in ("orc_gen_many_u32", "orc_gen_many_f32", "orc_gen_many_f64"):
@@ -124,9 +128,10 @@ class State:
             lib().orc_seed(self.gen, ctypes.c_uint64(seed), self.buf)
 
     @classmethod
-    def stream(cls, gen, seed: int, k: int) -> "State":
+    def stream(cls, gen, seed: int, k: int, variant: int = 0) -> "State":
         st = cls(gen, seed)
-        lib().orc_stream(st.gen, ctypes.c_uint64(seed), ctypes.c_uint64(k), st.buf)
+        if lib().orc_stream_v(st.gen, ctypes.c_uint64(seed), variant, ctypes.c_uint64(k), st.buf):
+            raise ValueError("no such stream variant")
         return st
 
     def copy(self) -> "State":
@@ -158,10 +163,17 @@ class State:
         return out
 
 
-def block_length(gen) -> int:
+def block_length(gen, variant: int = 0) -> int:
+    return variant_info(gen, variant)[1]
+
+
+def variant_info(gen, variant: int):
+    """(number of sequences, block length) of a Table 4 variant, or None."""
     arr = (ctypes.c_uint64 * NBIG)()
-    lib().orc_block_length(gid(gen), arr)
-    return sum(int(arr[i]) << (64 * i) for i in range(NBIG))
+    nmax = ctypes.c_uint64()
+    if lib().orc_variant(gid(gen), variant, ctypes.byref(nmax), arr):
+        return None
+    return nmax.value, sum(int(arr[i]) << (64 * i) for i in range(NBIG))
 
 
 def gm_param(gen, name: str) -> int:
@@ -175,13 +187,13 @@ def gm_param(gen, name: str) -> int:
 class Streams:
     """States of streams first..first+n-1 (back to back) for bulk generation."""
 
-    def __init__(self, gen, seed: int, first: int, n: int):
+    def __init__(self, gen, seed: int, first: int, n: int, variant: int = 0):
         self.gen = gid(gen)
         self.n = n
         self.sb = lib().orc_state_bytes(self.gen)
         self.buf = ctypes.create_string_buffer(self.sb * n)
-        rc = lib().orc_stream_range(self.gen, ctypes.c_uint64(seed), ctypes.c_uint64(first),
-                                    ctypes.c_uint64(n), self.buf)
+        rc = lib().orc_stream_range_v(self.gen, ctypes.c_uint64(seed), variant, ctypes.c_uint64(first),
+                                      ctypes.c_uint64(n), self.buf)
         if rc:
             raise RuntimeError("oracle stream range failed")
 

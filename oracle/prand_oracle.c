@@ -32,10 +32,16 @@
  *   Floats    Sec. 7.3 says only "uniform in [0,1)"; reading:
  *             f32 = (u >> 8) * 2^-24, f64 = u * 2^-32, MRG f64 = z * RN(1/(m1+1)).
  *
+ *   Variants  Table 4 lists up to three stream-initialisation variants per
+ *             generator (short / medium / long sequences); each is the pair
+ *             (number of sequences, block length L) of orc_variant(); the
+ *             GM/GQ ensemble of a variant spaces its points by that variant's
+ *             N_max L (reading); LFSR113 long: L = 2^80 (reading: >= 1e24).
+ *
  * Parity unpinned (readings of gaps in the paper, pinned only by invariants):
  *   the GM/GQ output map, ensemble size, seeding and block lengths; the MRG32K3A
  *   output map and default state; the LFSR113 default state and combination;
- *   the float conversions' exact form.
+ *   the float conversions' exact form; the variants' block lengths.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -660,7 +666,56 @@ static void gm_jump(int gen, gm_state *s, const uint64_t *e)
  * default seed, else SplitMix64 draws mod p (not both zero).  Point i is the
  * base advanced by i * D, D = nmax * L, so points never overlap below nmax
  * streams (Table 4: s * D <= period). */
-static void gm_seed(int gen, gm_state *s, uint64_t seed)
+/* Table 4: (number of sequences, block length) of the stream-initialisation
+ * variants: 0 = the default (init_sequence, or init_short_sequence), 1 =
+ * init_medium_sequence, 2 = init_long_sequence.  Block lengths are the printed
+ * maximal lengths (GM/GQ) or the powers of two above them (MRG32K3A 2^127,
+ * MT19937 2^432, LFSR113 2^34 and 2^80).  Returns -1 for a variant the table
+ * does not list. */
+int orc_variant(int gen, int v, uint64_t *nmax, uint64_t *L /* NBIG words */)
+{
+    memset(L, 0, NBIG * sizeof(uint64_t));
+    const u128 e7 = 10000000ull, e9 = 1000000000ull, e10 = 10000000000ull;
+    u128 l = 0;
+    uint64_t nm = 0;
+    switch (gen) {
+    case O_GM19: if (v == 0) { nm = 1000; l = 6000000; } break;
+    case O_GM29: case O_GQ58_1: case O_GQ58_3: case O_GQ58_4: {
+        const uint64_t f = gen == O_GQ58_3 ? 2 : gen == O_GQ58_4 ? 3 : 1;
+        if (v == 0) { nm = f * 100000000ull; l = 8 * e7; }
+        if (v == 1) { nm = f * 1000000ull; l = 8 * e9; }
+        if (v == 2) { nm = f * 10000ull; l = 8 * e9 * 100; }
+        break;
+    }
+    case O_GM31:
+        if (v == 0) { nm = 1000000000ull; l = 8 * e7; }
+        if (v == 1) { nm = 10000000ull; l = 8 * e9; }
+        if (v == 2) { nm = 100000ull; l = 8 * e9 * 100; }
+        break;
+    case O_GM55:
+        if (v == 0) { nm = 1000000000000000000ull; l = e10; }
+        if (v == 2) { nm = 4000000000ull; l = e10 * e10; }
+        break;
+    case O_GM61:
+        if (v == 0) { nm = 18000000000000000000ull; l = e10; }
+        if (v == 2) { nm = 4000000000ull; l = 3 * e10 * e10 * 100000; }
+        break;
+    case O_LFSR113:
+        if (v == 0) { nm = 3800000000000000000ull; l = (u128)1 << 34; }
+        if (v == 2) { nm = 4000000000ull; l = (u128)1 << 80; }
+        break;
+    case O_MRG32K3A: if (v == 0) { nm = 10000000000000000000ull; L[1] = 1ull << 63; if (nmax) *nmax = nm; return 0; } break;
+    case O_MT19937: if (v == 0) { nm = 10000000000000000000ull; L[432 / 64] = 1ull << (432 % 64); if (nmax) *nmax = nm; return 0; } break;
+    default: break;
+    }
+    if (!nm) return -1;
+    L[0] = (uint64_t)l;
+    L[1] = (uint64_t)(l >> 64);
+    if (nmax) *nmax = nm;
+    return 0;
+}
+
+static void gm_seed_v(int gen, int v, gm_state *s, uint64_t seed)
 {
     gm_params_t P; gm_params(gen, &P);
     uint64_t a = 1, b = 1;
@@ -669,9 +724,9 @@ static void gm_seed(int gen, gm_state *s, uint64_t seed)
         do { a = splitmix64(&sm) % P.p; b = splitmix64(&sm) % P.p; } while (!(a | b));
     }
     uint64_t x0 = a << P.t, x1 = b << P.t;
-    uint64_t D[NBIG] = { 0 }, Lw[NBIG] = { 0 };
-    Lw[0] = P.L;
-    big_mul_u64(D, Lw, P.nmax);
+    uint64_t D[NBIG] = { 0 }, Lw[NBIG] = { 0 }, nmax = 0;
+    orc_variant(gen, v, &nmax, Lw);
+    big_mul_u64(D, Lw, nmax);  /* point spacing of the variant's ensemble */
     memset(s, 0, sizeof *s);
     for (int i = 0; i < P.s; ++i) {
         uint64_t e[NBIG];
@@ -682,6 +737,8 @@ static void gm_seed(int gen, gm_state *s, uint64_t seed)
         gm_apply(&s->xp[i], &s->xc[i], m, P.g);
     }
 }
+
+static void gm_seed(int gen, gm_state *s, uint64_t seed) { gm_seed_v(gen, 0, s, seed); }
 
 /* Reading of the output: every point takes one step (eq. (rec1)); word =
  * sum_i strip_i << (v*i), truncated to 32 bits, point 0 least significant. */
@@ -742,42 +799,41 @@ int orc_jump(int gen, void *st, const uint64_t *e)
 /* Block length L of the stream-initialisation variant (Table 4; reading:
  * GM/GQ take the printed maximal length, MRG32K3A 2^127 >= 1e38, MT19937
  * 2^432 >= 1e130, LFSR113 2^34 >= 1e10). */
-int orc_block_length(int gen, uint64_t *L /* NBIG words */)
-{
-    memset(L, 0, NBIG * sizeof(uint64_t));
-    if (gen == O_MT19937) { L[432 / 64] = 1ull << (432 % 64); return 0; }
-    if (gen == O_MRG32K3A) { L[1] = 1ull << 63; return 0; }
-    if (gen == O_LFSR113) { L[0] = 1ull << 34; return 0; }
-    gm_params_t P;
-    if (gm_params(gen, &P)) return -1;
-    L[0] = P.L;
-    return 0;
-}
+int orc_block_length(int gen, uint64_t *L /* NBIG words */) { return orc_variant(gen, 0, NULL, L); }
 
-/* Stream k under block splitting: the seeded state advanced by k * L. */
-int orc_stream(int gen, uint64_t seed, uint64_t k, void *st)
+/* Stream k of variant v under block splitting: the variant's seeded state
+ * (for GM/GQ, the ensemble spaced for that variant) advanced by k * L_v. */
+int orc_stream_v(int gen, uint64_t seed, int v, uint64_t k, void *st)
 {
     uint64_t L[NBIG], e[NBIG];
-    if (orc_seed(gen, seed, st)) return -1;
-    orc_block_length(gen, L);
+    if (orc_variant(gen, v, NULL, L)) return -1;
+    if (is_gm(gen)) gm_seed_v(gen, v, st, seed);
+    else if (orc_seed(gen, seed, st)) return -1;
     big_mul_u64(e, L, k);
     return orc_jump(gen, st, e);
 }
 
-/* States of streams first..first+n-1, laid out back to back: stream first
- * by its own jump, every later one by one more jump of L from the previous. */
-int orc_stream_range(int gen, uint64_t seed, uint64_t first, uint64_t n, void *out)
+int orc_stream(int gen, uint64_t seed, uint64_t k, void *st) { return orc_stream_v(gen, seed, 0, k, st); }
+
+/* States of streams first..first+n-1 of variant v, laid out back to back:
+ * stream first by its own jump, every later one by one more jump of L_v. */
+int orc_stream_range_v(int gen, uint64_t seed, int v, uint64_t first, uint64_t n, void *out)
 {
     int sb = orc_state_bytes(gen);
     if (sb < 0) return -1;
     uint64_t L[NBIG];
-    orc_block_length(gen, L);
+    if (orc_variant(gen, v, NULL, L)) return -1;
     uint8_t *o = out;
     for (uint64_t j = 0; j < n; ++j) {
-        if (j == 0) { if (orc_stream(gen, seed, first, o)) return -1; }
+        if (j == 0) { if (orc_stream_v(gen, seed, v, first, o)) return -1; }
         else { memcpy(o + j * sb, o + (j - 1) * sb, (size_t)sb); orc_jump(gen, o + j * sb, L); }
     }
     return 0;
+}
+
+int orc_stream_range(int gen, uint64_t seed, uint64_t first, uint64_t n, void *out)
+{
+    return orc_stream_range_v(gen, seed, 0, first, n, out);
 }
 
 void orc_gen_u32(int gen, void *st, uint32_t *out, uint64_t n)
