@@ -100,6 +100,24 @@ prand_status_t prand_create(prand_handle_t *h, prand_gen_t gen, uint64_t seed);
  * PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
 prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams);
 
+/* The same with a stream-initialisation variant of Table 4:
+ * PRAND_VARIANT_DEFAULT (init_sequence / init_short_sequence, the one
+ * prand_init_streams uses), PRAND_VARIANT_MEDIUM (init_medium_sequence) or
+ * PRAND_VARIANT_LONG (init_long_sequence).  A variant trades the number of
+ * streams for their length: stream k starts k * L_v outputs after the base,
+ * with (N_max, L_v) the variant's row of Table 4 (block length: the printed
+ * maximal length for GM/GQ, 2^80 for LFSR113 long); for GM/GQ the base
+ * ensemble's points are spaced N_max L_v apart, so each variant has its own
+ * base.  Medium exists for GM29, GM31 and GQ58.x; long for those and GM55,
+ * GM61, LFSR113; MRG32K3A and MT19937 have the default only.
+ * Errors: as prand_init_streams, and PRAND_ERR_ARG for a variant Table 4 does
+ * not list for the generator. */
+#define PRAND_VARIANT_DEFAULT 0
+#define PRAND_VARIANT_MEDIUM 1
+#define PRAND_VARIANT_LONG 2
+prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uint64_t first_stream,
+                                          uint64_t n_streams);
+
 /* Write the next n_per_stream outputs of every stream, stream-major:
  * dev_out[j * n_per_stream + i] = output i of stream j (rng_generate_gpu_array_,
  * Sec. 6).  Each stream continues where the previous generate call on the
@@ -135,7 +153,7 @@ prand_status_t prand_generate_host_f32(prand_handle_t h, float *host_out, uint64
 prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint64_t n_per_stream, prand_stream_t stream);
 
 /* The streams as single-stream states for user code (prand_device.h, the
- * paper's single-threaded interface, Sec. 7.4): prand_export_states writes
+ * paper's single-threaded interface, Sec. 7.3): prand_export_states writes
  * one struct per stream, stream j at index j (prand_mt19937_state,
  * prand_mrg32k3a_state, prand_lfsr113_state or prand_gm_state, of
  * prand_device_state_bytes(gen) bytes each), at the streams' current
@@ -158,6 +176,13 @@ prand_status_t prand_import_states(prand_handle_t h, const void *dev_states, pra
  * (rng_skipahead_, Sec. 7.2; jump methods of Sec. 5.1-5.4).
  * Errors: PRAND_ERR_ARG, PRAND_ERR_STATE (no streams), PRAND_ERR_CUDA. */
 prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4]);
+
+/* Advance every stream by a * 2^b outputs (the paper's MT19937 skip-ahead
+ * form, N = a 2^b < 2^512, Sec. 7.9); for MT19937 a 2^b may reach 2^512, for
+ * the other generators it must stay below 2^256 (it is then prand_skipahead
+ * with that offset).  a = 0 is a no-op.  Returns after the work completes.
+ * Errors: PRAND_ERR_ARG (out of range), PRAND_ERR_STATE, PRAND_ERR_CUDA. */
+prand_status_t prand_skipahead_pow2(prand_handle_t h, uint64_t a, uint32_t b);
 
 /* Copy the full state of all streams into a host buffer (checkpoint), as a
  * versioned blob that prand_set_state accepts on a handle of the same

@@ -1,5 +1,5 @@
 /* Single-stream generation inside user code (host or device): the paper's
- * single-threaded interface (Sec. 7.4, rng_generate_ and
+ * single-threaded interface (Sec. 7.3, rng_generate_ and
  * rng_generate_uniform_float_), one state per stream, one output per call.
  *
  * Header-only C++.  Under nvcc every function is __host__ __device__, so a

@@ -39,7 +39,7 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
            "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
            "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
-           "prand_import_states"]
+           "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2"]
 
 
 class PrandError(RuntimeError):
@@ -78,6 +78,8 @@ def load(build_if_missing: bool = False):
     u64 = ctypes.c_uint64
     L.prand_create.argtypes = [ctypes.POINTER(H), ctypes.c_int, u64]
     L.prand_init_streams.argtypes = [H, u64, u64]
+    L.prand_init_streams_variant.argtypes = [H, ctypes.c_int32, u64, u64]
+    L.prand_skipahead_pow2.argtypes = [H, u64, ctypes.c_uint32]
     for nm in ("prand_generate_u32", "prand_generate_f32", "prand_generate_f64", "prand_generate_host_u32",
                "prand_generate_host_f32", "prand_generate_host_f64"):
         getattr(L, nm).argtypes = [H, ctypes.c_void_p, u64, ctypes.c_void_p]
@@ -186,6 +188,18 @@ def prand_export_states(h: int, dev_states: int, stream: int = 0) -> None:
 
 def prand_import_states(h: int, dev_states: int, stream: int = 0) -> None:
     _check(load().prand_import_states(h, dev_states, stream), "prand_import_states")
+
+
+VARIANT_DEFAULT, VARIANT_MEDIUM, VARIANT_LONG = 0, 1, 2
+
+
+def prand_init_streams_variant(h: int, variant: int, first: int, n: int) -> int:
+    """Streams first..first+n-1 of a Table 4 variant; returns the status (7 = overlap warning)."""
+    return _check(load().prand_init_streams_variant(h, variant, first, n), "prand_init_streams_variant", allow_warn=True)
+
+
+def prand_skipahead_pow2(h: int, a: int, b: int) -> None:
+    _check(load().prand_skipahead_pow2(h, ctypes.c_uint64(a), b), "prand_skipahead_pow2")
 
 
 def prand_skipahead(h: int, offset: int) -> None:

@@ -357,7 +357,7 @@ prand_status_t engine_bases(Engine &E, uint64_t seed, cudaStream_t st, const See
     for (int g = 0; g < PRAND_NUM_GENERATORS && s == PRAND_OK; ++g) {
         void *p = (char *)B.dev + B.off[g];
         if (g == PRAND_MT19937) s = mt_seed(seed, p, st);
-        else if (is_gm(g)) s = gm_seed(g, E.T, seed, p, st);
+        else if (is_gm(g)) { Variant V; variant_params(g, 0, &V); s = gm_seed(g, E.T, seed, V, p, st); }
         else s = mrg_lfsr_seed(g, seed, p, st);
     }
     // wait once, so later batches on any stream see the bases
@@ -763,10 +763,14 @@ prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n
             s = mt_init(T, ctx.base[r.gen], a, r.stream, 1, st);
             if (s == PRAND_OK) s = mt_gen(a, 1, &idx, r.dev_out, r.dtype, r.length, st);
         } else if (is_gm(r.gen)) {
-            s = gm_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
+            Variant V;
+            variant_params(r.gen, 0, &V);
+            s = gm_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, V, st);
             if (s == PRAND_OK) s = gm_gen(r.gen, T, a, b, R, r.dev_out, r.dtype, r.length, st);
         } else {
-            s = mrg_lfsr_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, st);
+            Variant V;
+            variant_params(r.gen, 0, &V);
+            s = mrg_lfsr_init(r.gen, T, ctx.base[r.gen], a, r.stream, 1, V, st);
             if (s == PRAND_OK) s = mrg_lfsr_gen(r.gen, T, a, b, R, r.dev_out, r.dtype, r.length, st);
         }
     }

@@ -27,6 +27,56 @@ size_t state_bytes_per_stream(int gen)
     return 2 * (size_t)gm_params(gen).s * sizeof(uint64_t);
 }
 
+bool variant_params(int gen, int v, Variant *out)
+{
+    // Table 4: (number of sequences, maximal length) of each initialisation
+    // function; the block length is the printed maximal length for GM/GQ and
+    // the power of two above it for LFSR113 (2^34, 2^80).
+    using u128 = unsigned __int128;
+    const u128 e7 = 10000000ull, e9 = 1000000000ull, e10 = 10000000000ull;
+    uint64_t nm = 0;
+    u128 L = 0;
+    switch (gen) {
+    case PRAND_GM19: if (v == 0) { nm = 1000; L = 6000000; } break;
+    case PRAND_GM29: case PRAND_GQ58_1: case PRAND_GQ58_3: case PRAND_GQ58_4: {
+        const uint64_t f = gen == PRAND_GQ58_3 ? 2 : gen == PRAND_GQ58_4 ? 3 : 1;
+        if (v == 0) { nm = f * 100000000ull; L = 8 * e7; }
+        else if (v == 1) { nm = f * 1000000ull; L = 8 * e9; }
+        else if (v == 2) { nm = f * 10000ull; L = 800 * e9; }
+        break;
+    }
+    case PRAND_GM31:
+        if (v == 0) { nm = 1000000000ull; L = 8 * e7; }
+        else if (v == 1) { nm = 10000000ull; L = 8 * e9; }
+        else if (v == 2) { nm = 100000ull; L = 800 * e9; }
+        break;
+    case PRAND_GM55:
+        if (v == 0) { nm = 1000000000000000000ull; L = e10; }
+        else if (v == 2) { nm = 4000000000ull; L = e10 * e10; }
+        break;
+    case PRAND_GM61:
+        if (v == 0) { nm = 18000000000000000000ull; L = e10; }
+        else if (v == 2) { nm = 4000000000ull; L = 300000 * e10 * e10; }
+        break;
+    case PRAND_LFSR113:
+        if (v == 0) { nm = 3800000000000000000ull; L = (u128)1 << 34; }
+        else if (v == 2) { nm = 4000000000ull; L = (u128)1 << 80; }
+        break;
+    case PRAND_MRG32K3A: case PRAND_MT19937:
+        if (v == 0) nm = 10000000000000000000ull;  // L = 2^127 / 2^432, applied as shifts
+        break;
+    default: break;
+    }
+    if (!nm) return false;
+    out->nmax = nm;
+    out->L[0] = (uint64_t)L;
+    out->L[1] = (uint64_t)(L >> 64);
+    const u128 D = L * nm;  // below 2^117 for every GM/GQ variant
+    out->D[0] = is_gm(gen) ? (uint64_t)D : 0;
+    out->D[1] = is_gm(gen) ? (uint64_t)(D >> 64) : 0;
+    return true;
+}
+
 uint64_t table4_nmax(int gen)
 {
     if (gen == PRAND_MT19937 || gen == PRAND_MRG32K3A) return 10000000000000000000ull;  // 1e19
@@ -102,6 +152,8 @@ struct prand_handle_s {
     void *d_spare = nullptr;
     uint64_t first = 0, n = 0;
     uint64_t position = 0;
+    int variant = 0;       // Table 4 variant of the streams
+    int base_variant = 0;  // variant the base state was seeded for (GM/GQ ensembles differ)
     uint32_t mt_idx = kMtN;
     cudaStream_t last_stream = 0;
     // host fills: two device staging buffers, a copy stream and its events
@@ -114,13 +166,15 @@ struct prand_handle_s {
 namespace {
 
 constexpr uint32_t kBlobMagic = 0x444E5250u;  // "PRND"
-constexpr uint32_t kBlobVersion = 1;
+constexpr uint32_t kBlobVersion = 2;  // 2: the stream variant follows the state sizes
 
 struct BlobHeader {
     uint32_t magic, version;
     int32_t gen;
     uint32_t mt_idx;
     uint64_t seed, first, n, position, state_bytes;
+    int32_t variant;
+    uint32_t reserved;
 };
 
 prand_status_t check_device(prand_handle_t h)
@@ -305,8 +359,10 @@ prand_status_t prand_create(prand_handle_t *out, prand_gen_t gen, uint64_t seed)
     prand_status_t s = get_tables(h->gen, &h->T);
     if (s != PRAND_OK) { delete h; return s; }
     if (cudaMalloc(&h->d_base, state_bytes_per_stream(h->gen)) != cudaSuccess) { delete h; return PRAND_ERR_NOMEM; }
+    Variant V;
+    variant_params(h->gen, 0, &V);
     if (h->gen == PRAND_MT19937) s = mt_seed(seed, h->d_base, 0);
-    else if (is_gm(h->gen)) s = gm_seed(h->gen, h->T, seed, h->d_base, 0);
+    else if (is_gm(h->gen)) s = gm_seed(h->gen, h->T, seed, V, h->d_base, 0);
     else s = mrg_lfsr_seed(h->gen, seed, h->d_base, 0);
     if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
     if (s != PRAND_OK) { cudaFree(h->d_base); delete h; return s; }
@@ -314,14 +370,22 @@ prand_status_t prand_create(prand_handle_t *out, prand_gen_t gen, uint64_t seed)
     return PRAND_OK;
 }
 
-prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams)
+prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uint64_t first_stream, uint64_t n_streams)
 {
     if (!h || n_streams == 0) return PRAND_ERR_ARG;
+    Variant V;
+    if (!variant_params(h->gen, variant, &V)) return PRAND_ERR_ARG;
     uint64_t last;
     if (__builtin_add_overflow(first_stream, n_streams - 1, &last)) return PRAND_ERR_ARG;
     prand_status_t s = check_device(h);
     if (s != PRAND_OK) return s;
     if ((s = sync_last(h)) != PRAND_OK) return s;
+    if (is_gm(h->gen) && variant != h->base_variant) {
+        // the GM/GQ ensemble is spaced for its variant: seed the base again
+        if ((s = gm_seed(h->gen, h->T, h->seed, V, h->d_base, 0)) != PRAND_OK) return s;
+        h->base_variant = variant;
+    }
+    h->variant = variant;
     free_states(h);
     uint64_t bytes;
     if (mul_overflows(n_streams, state_bytes_per_stream(h->gen), &bytes)) return PRAND_ERR_ARG;
@@ -332,8 +396,8 @@ prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint6
         return PRAND_ERR_NOMEM;
     }
     if (h->gen == PRAND_MT19937) s = mt_init(h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
-    else if (is_gm(h->gen)) s = gm_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
-    else s = mrg_lfsr_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
+    else if (is_gm(h->gen)) s = gm_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, V, 0);
+    else s = mrg_lfsr_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, V, 0);
     if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
     if (s != PRAND_OK) { free_states(h); return s; }
     h->first = first_stream;
@@ -342,8 +406,13 @@ prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint6
     h->mt_idx = kMtN;
     h->last_stream = 0;
     // Table 4 capacity: the last stream index must stay below the number of sequences
-    if (last >= table4_nmax(h->gen)) return PRAND_WARN_STREAM_OVERLAP;
+    if (last >= V.nmax) return PRAND_WARN_STREAM_OVERLAP;
     return PRAND_OK;
+}
+
+prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams)
+{
+    return prand_init_streams_variant(h, 0, first_stream, n_streams);
 }
 
 prand_status_t prand_generate_u32(prand_handle_t h, uint32_t *dev_out, uint64_t n_per_stream, prand_stream_t stream)
@@ -423,6 +492,26 @@ prand_status_t prand_skipahead(prand_handle_t h, const uint64_t offset_le[4])
     return s;
 }
 
+prand_status_t prand_skipahead_pow2(prand_handle_t h, uint64_t a, uint32_t b)
+{
+    if (!h) return PRAND_ERR_ARG;
+    if (a == 0) return PRAND_OK;
+    const uint32_t bits = b + (64 - (uint32_t)__builtin_clzll(a));  // bit length of a 2^b
+    if (b >= 512 || bits > (h->gen == PRAND_MT19937 ? 512u : 256u)) return PRAND_ERR_ARG;
+    uint64_t w[8] = {};
+    w[b / 64] = a << (b % 64);
+    if (b % 64 && b / 64 + 1 < 8) w[b / 64 + 1] = a >> (64 - b % 64);
+    if (h->gen != PRAND_MT19937) return prand_skipahead(h, w);
+    if (!h->d_state || h->n == 0) return PRAND_ERR_STATE;
+    prand_status_t s = check_device(h);
+    if (s != PRAND_OK) return s;
+    if ((s = sync_last(h)) != PRAND_OK) return s;
+    s = mt_skip512(h->T, h->d_state, h->n, &h->mt_idx, w, 0);
+    if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
+    if (s == PRAND_OK) h->position += w[0];
+    return s;
+}
+
 prand_status_t prand_get_state(prand_handle_t h, void *host_buf, size_t *bytes)
 {
     if (!h || !bytes) return PRAND_ERR_ARG;
@@ -434,7 +523,7 @@ prand_status_t prand_get_state(prand_handle_t h, void *host_buf, size_t *bytes)
     prand_status_t s = check_device(h);
     if (s != PRAND_OK) return s;
     if ((s = sync_last(h)) != PRAND_OK) return s;
-    BlobHeader hd = { kBlobMagic, kBlobVersion, h->gen, h->mt_idx, h->seed, h->first, h->n, h->position, sb };
+    BlobHeader hd = { kBlobMagic, kBlobVersion, h->gen, h->mt_idx, h->seed, h->first, h->n, h->position, sb, h->variant, 0 };
     memcpy(host_buf, &hd, sizeof hd);
     if (cudaMemcpy((char *)host_buf + sizeof hd, h->d_state, sb, cudaMemcpyDeviceToHost) != cudaSuccess) return PRAND_ERR_CUDA;
     *bytes = need;
@@ -446,7 +535,10 @@ prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t by
     if (!h || !host_buf || bytes < sizeof(BlobHeader)) return PRAND_ERR_ARG;
     BlobHeader hd;
     memcpy(&hd, host_buf, sizeof hd);
-    if (hd.magic != kBlobMagic || hd.version != kBlobVersion || hd.gen != h->gen || hd.n == 0) return PRAND_ERR_STATE;
+    Variant V;
+    if (hd.magic != kBlobMagic || hd.version != kBlobVersion || hd.gen != h->gen || hd.n == 0 ||
+        !variant_params(h->gen, hd.variant, &V))
+        return PRAND_ERR_STATE;
     uint64_t sb;
     if (mul_overflows(hd.n, state_bytes_per_stream(h->gen), &sb) || sb != hd.state_bytes ||
         bytes != sizeof hd + sb || hd.mt_idx > (uint32_t)kMtN)
@@ -468,6 +560,7 @@ prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t by
     h->n = hd.n;
     h->position = hd.position;
     h->mt_idx = hd.mt_idx;
+    h->variant = hd.variant;
     return PRAND_OK;
 }
 

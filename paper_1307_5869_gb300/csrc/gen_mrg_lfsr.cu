@@ -169,14 +169,23 @@ __global__ void lfsr_seed_kernel(uint32_t *base, uint64_t seed)
     }
 }
 
-__global__ void lfsr_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n)
+// Stream j = base advanced by (first + j) * L, L of 128 bits (2^34 or 2^80);
+// the exponent of up to 192 bits is exact.
+__global__ void lfsr_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n,
+                                 uint64_t llo, uint64_t lhi)
 {
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     uint32_t z[4] = { base[0], base[1], base[2], base[3] };
-    uint64_t k = first + j;
-    for (int b = 0; b < 64; ++b)
-        if ((k >> b) & 1u) lfsr_apply_bit(tab, kLfsrStreamShift + b, z);
+    const uint64_t k = first + j;
+    uint64_t e[3];
+    e[0] = k * llo;
+    const uint64_t c0 = __umul64hi(k, llo);
+    e[1] = k * lhi + c0;
+    e[2] = __umul64hi(k, lhi) + (e[1] < c0 ? 1u : 0u);
+    for (int w = 0; w < 3; ++w)
+        for (int b = 0; e[w] && b < 64; ++b)
+            if ((e[w] >> b) & 1u) lfsr_apply_bit(tab, 64 * w + b, z);
     for (int c = 0; c < 4; ++c) state[c * n + j] = z[c];
 }
 
@@ -272,13 +281,14 @@ prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t 
 }
 
 prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                             cudaStream_t st)
+                             const Variant &V, cudaStream_t st)
 {
     const unsigned B = 128;
     if (gen == PRAND_MRG32K3A)
         mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
     else
-        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+        lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n,
+                                                       V.L[0], V.L[1]);
     return launch_check();
 }
 

@@ -164,28 +164,38 @@ prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, ui
 }
 
 // Skip ahead: consume the rest of the current block, then jump by polynomials.
-prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off_in, cudaStream_t st)
+// Every stream += off (512 bits, off < 2^512 as for the paper's a 2^b form):
+// the rest of the current block is used up by moving the index, the remainder
+// is one polynomial x^(2^b) mod phi per set bit.
+prand_status_t mt_skip512(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const uint64_t off_in[8],
+                          cudaStream_t st)
 {
-    U256 off = off_in;
+    MtBits e = {};
+    for (int i = 0; i < 8; ++i) e.w[i] = off_in[i];
     if (*idx < (uint32_t)kMtN) {
         uint64_t rem = kMtN - *idx;
-        bool small = !off.w[1] && !off.w[2] && !off.w[3];
-        if (small && off.w[0] < rem) { *idx += (uint32_t)off.w[0]; return PRAND_OK; }
+        bool small = true;
+        for (int i = 1; i < 8; ++i) small = small && !e.w[i];
+        if (small && e.w[0] < rem) { *idx += (uint32_t)e.w[0]; return PRAND_OK; }
         uint64_t borrow = rem;
-        for (int i = 0; i < 4 && borrow; ++i) {
-            uint64_t before = off.w[i];
-            off.w[i] -= borrow;
+        for (int i = 0; i < 8 && borrow; ++i) {
+            uint64_t before = e.w[i];
+            e.w[i] -= borrow;
             borrow = before < borrow ? 1 : 0;
         }
         *idx = kMtN;
     }
-    MtBits e = {};
-    for (int i = 0; i < 4; ++i) e.w[i] = off.w[i];
     bool any = false;
-    for (int i = 0; i < 4; ++i) any = any || e.w[i];
+    for (int i = 0; i < 8; ++i) any = any || e.w[i];
     if (!any) return PRAND_OK;
     mt_multi_kernel<<<grid_warps(n), 32 * kMtWarpsPerBlock, 0, st>>>(T->mt, (uint32_t *)d_state, n, e, nullptr);
     return launch_check();
+}
+
+prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st)
+{
+    const uint64_t w[8] = { off.w[0], off.w[1], off.w[2], off.w[3], 0, 0, 0, 0 };
+    return mt_skip512(T, d_state, n, idx, w, st);
 }
 
 prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st)

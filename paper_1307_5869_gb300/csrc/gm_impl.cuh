@@ -225,9 +225,10 @@ __device__ __forceinline__ void gm_apply(const uint64_t *M, uint64_t &zc, uint64
     zc = c; zp = q;
 }
 
-// Jump by the 128-bit exponent (hi, lo).
+// Jump by the 128-bit exponent (hi, lo), and by a third word w2 (bits 128..191).
 template <int GEN>
-__device__ __forceinline__ void gm_jump128(const uint64_t *tab, uint64_t lo, uint64_t hi, uint64_t &zc, uint64_t &zp)
+__device__ __forceinline__ void gm_jump128(const uint64_t *tab, uint64_t lo, uint64_t hi, uint64_t &zc, uint64_t &zp,
+                                           uint64_t w2 = 0)
 {
 #pragma unroll 1
     for (int b = 0; b < 64; ++b)
@@ -235,6 +236,9 @@ __device__ __forceinline__ void gm_jump128(const uint64_t *tab, uint64_t lo, uin
 #pragma unroll 1
     for (int b = 0; b < 64; ++b)
         if ((hi >> b) & 1u) gm_apply<GEN>(tab + 4 * (64 + b), zc, zp);
+#pragma unroll 1
+    for (int b = 0; w2 && b < 64; ++b)
+        if ((w2 >> b) & 1u) gm_apply<GEN>(tab + 4 * (128 + b), zc, zp);
 }
 
 __device__ __forceinline__ void mul64x64(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
@@ -243,9 +247,9 @@ __device__ __forceinline__ void mul64x64(uint64_t a, uint64_t b, uint64_t &lo, u
     hi = __umul64hi(a, b);
 }
 
-// Base ensemble: lane i < s gets the base pair advanced by i * D.
+// Base ensemble: lane i < s gets the base pair advanced by i * D (D: 128 bits).
 template <int GEN>
-__global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t seed)
+__global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t seed, uint64_t dlo, uint64_t dhi)
 {
     using P = GmT<GEN>;
     int i = threadIdx.x;
@@ -256,9 +260,7 @@ __global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t see
         do { a = splitmix64_next(sm) % P::p; b = splitmix64_next(sm) % P::p; } while (!(a | b));
     }
     uint64_t zp = a, zc = b;  // (z^(0), z^(1))
-    // e = i * nmax * L, as a 128-bit product (nmax * L < 2^98, i < 32)
-    uint64_t dlo, dhi;
-    mul64x64(P::nmax, P::L_, dlo, dhi);
+    // e = i * D as 128 bits (s D fits inside the period p^2 - 1 < 2^122)
     uint64_t elo, ehi;
     mul64x64(dlo, (uint64_t)i, elo, ehi);
     ehi += dhi * (uint64_t)i;
@@ -267,18 +269,24 @@ __global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t see
     base[P::s + i] = zc << P::t;   // x^(n)
 }
 
-// Stream j of the handle = base advanced by (first + j) * L.  One group per stream.
+// Stream j of the handle = base advanced by (first + j) * L, L of 128 bits (the
+// exponent, of up to 192 bits, is exact).  One group per stream.
 template <int GEN>
-__global__ void gm_init_kernel(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n)
+__global__ void gm_init_kernel(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n,
+                               uint64_t llo, uint64_t lhi)
 {
     using P = GmT<GEN>;
     uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / P::lanes;
     int i = threadIdx.x % P::lanes;
     if (g >= n || i >= P::s) return;
     uint64_t zp = base[i] >> P::t, zc = base[P::s + i] >> P::t;
-    uint64_t elo, ehi;
-    mul64x64(first + g, P::L_, elo, ehi);
-    gm_jump128<GEN>(tab, elo, ehi, zc, zp);
+    const uint64_t k = first + g;
+    uint64_t e0, c0, e1, c1;
+    mul64x64(k, llo, e0, c0);
+    mul64x64(k, lhi, e1, c1);
+    e1 += c0;
+    const uint64_t e2 = c1 + (e1 < c0 ? 1u : 0u);
+    gm_jump128<GEN>(tab, e0, e1, zc, zp, e2);
     state[g * P::s + i] = zp << P::t;
     state[(n + g) * P::s + i] = zc << P::t;
 }
@@ -421,16 +429,17 @@ inline unsigned gm_grid_for(uint64_t n, unsigned block) { return (unsigned)((n +
 
 template <int GEN>
 struct GmHost {
-    static prand_status_t seed(const uint64_t *tab, uint64_t *base, uint64_t seed, cudaStream_t st)
+    static prand_status_t seed(const uint64_t *tab, uint64_t *base, uint64_t seed, const Variant &V, cudaStream_t st)
     {
-        gm_seed_kernel<GEN><<<1, 32, 0, st>>>(tab, base, seed);
+        gm_seed_kernel<GEN><<<1, 32, 0, st>>>(tab, base, seed, V.D[0], V.D[1]);
         return launch_check();
     }
     static prand_status_t init(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n,
-                               cudaStream_t st)
+                               const Variant &V, cudaStream_t st)
     {
         const unsigned B = 128;
-        gm_init_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, base, state, first, n);
+        gm_init_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, base, state, first, n, V.L[0],
+                                                                               V.L[1]);
         return launch_check();
     }
     static prand_status_t skip(const uint64_t *tab, uint64_t *state, uint64_t n, const U256 &off, cudaStream_t st)
@@ -479,14 +488,15 @@ struct GmHost {
 // Per-generator entry points, instantiated one translation unit per generator.
 #define PRAND_GM_INSTANTIATE(GEN, NAME)                                                                          \
     prand_status_t NAME##_table(uint64_t *tab, cudaStream_t st) { return gm_build_table_t<GEN>(tab, st); }      \
-    prand_status_t NAME##_seed(const uint64_t *tab, uint64_t *base, uint64_t seed, cudaStream_t st)            \
+    prand_status_t NAME##_seed(const uint64_t *tab, uint64_t *base, uint64_t seed, const Variant &V,           \
+                               cudaStream_t st)                                                               \
     {                                                                                                         \
-        return GmHost<GEN>::seed(tab, base, seed, st);                                                        \
+        return GmHost<GEN>::seed(tab, base, seed, V, st);                                                     \
     }                                                                                                         \
     prand_status_t NAME##_init(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first,     \
-                               uint64_t n, cudaStream_t st)                                                   \
+                               uint64_t n, const Variant &V, cudaStream_t st)                                 \
     {                                                                                                         \
-        return GmHost<GEN>::init(tab, base, state, first, n, st);                                             \
+        return GmHost<GEN>::init(tab, base, state, first, n, V, st);                                          \
     }                                                                                                         \
     prand_status_t NAME##_skip(const uint64_t *tab, uint64_t *state, uint64_t n, const U256 &off,             \
                                cudaStream_t st)                                                               \

@@ -57,6 +57,20 @@ const GmParams &gm_params(int gen);
 // Block length L as a 64-bit value for GM/GQ and the Table 4 capacity per generator.
 uint64_t table4_nmax(int gen);
 
+// A stream-initialisation variant of Table 4 (0: init_sequence or
+// init_short_sequence, 1: init_medium_sequence, 2: init_long_sequence): its
+// number of sequences, block length L and, for GM/GQ, the spacing D = N_max L
+// of the ensemble's points, the last two as 128-bit little-endian values.
+// MRG32K3A and MT19937 have variant 0 only, with L = 2^127 and 2^432 (not
+// representable here; their kernels use the shift).  False if Table 4 does not
+// list the variant.
+struct Variant {
+    uint64_t nmax = 0;
+    uint64_t L[2] = { 0, 0 };
+    uint64_t D[2] = { 0, 0 };
+};
+bool variant_params(int gen, int v, Variant *out);
+
 // ---------------------------------------------------------------------------
 // Per-device jump tables.
 // ---------------------------------------------------------------------------
@@ -146,19 +160,21 @@ prand_status_t lfsr_build_table(uint32_t *tab, cudaStream_t st);
 prand_status_t gm_build_table(int gen, uint64_t *tab, cudaStream_t st);
 prand_status_t mrg_lfsr_seed(int gen, uint64_t seed, void *d_base, cudaStream_t st);
 prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                             cudaStream_t st);
+                             const Variant &V, cudaStream_t st);
 prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
 prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out,
                             int dtype, uint64_t nper, cudaStream_t st);
-prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, void *d_base, cudaStream_t st);
+prand_status_t gm_seed(int gen, const DevTables *T, uint64_t seed, const Variant &V, void *d_base, cudaStream_t st);
 prand_status_t gm_init(int gen, const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n,
-                       cudaStream_t st);
+                       const Variant &V, cudaStream_t st);
 prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, const U256 &off, cudaStream_t st);
 prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out, int dtype,
                       uint64_t nper, cudaStream_t st);
 prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
 prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
 prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st);
+prand_status_t mt_skip512(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const uint64_t off[8],
+                          cudaStream_t st);
 // MT19937 keeps its state as 624-word blocks per stream (a range is a pointer
 // offset); *idx, the position inside the block shared by all streams, advances.
 prand_status_t mt_gen(void *d_state, uint64_t nstreams, uint32_t *idx, void *out, int dtype, uint64_t nper, cudaStream_t st);

@@ -1,5 +1,5 @@
 // Export / import of a handle's stream states in the one-struct-per-stream
-// layout of prand_device.h (the paper's single-threaded state, Sec. 7.4).
+// layout of prand_device.h (the paper's single-threaded state, Sec. 7.3).
 #include "prand_internal.h"
 #include "prand_device.h"
 

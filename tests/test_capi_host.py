@@ -72,6 +72,8 @@ def test_argument_errors_without_device(lib):
     assert L.prand_import_states(None, vp(0x1000), None) == 1
     assert [L.prand_device_state_bytes(g) for g in range(11)] == [2500, 24, 16] + [512] * 8
     assert L.prand_device_state_bytes(11) == 0
+    assert L.prand_init_streams_variant(None, 0, 0, 1) == 1
+    assert L.prand_skipahead_pow2(None, 1, 0) == 1
 
 
 def test_binding_raises_on_error(lib):

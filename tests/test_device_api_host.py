@@ -1,5 +1,5 @@
 """The single-stream functions of include/prand_device.h (the paper's
-single-threaded interface, Sec. 7.4), compiled for the host: from a stream's
+single-threaded interface, Sec. 7.3), compiled for the host: from a stream's
 oracle state they produce the oracle's outputs, integer and float, bit for
 bit."""
 import ctypes
