@@ -24,6 +24,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The serving leg keeps up to 32 batches in flight, each on its own stream; with
+# the default 8 hardware queues, streams would share queues and a long batch
+# would hold up unrelated ones.  Takes effect only before CUDA starts.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from paper_1307_5869_gb300 import workloads as W  # noqa: E402
 

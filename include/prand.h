@@ -298,7 +298,11 @@ typedef struct {
 /* output_bytes: device arena for outputs (a request whose output does not fit
  * is refused at submit); slots_per_generator: resident streams per generator.
  * The server is bound to the current device; its worker thread makes that
- * device current itself.  Errors: PRAND_ERR_ARG, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+ * device current itself.  It keeps up to 32 batches in flight, each on its own
+ * stream; the process should set CUDA_DEVICE_MAX_CONNECTIONS=32 (the driver
+ * default is 8) before CUDA starts, or flights that share a hardware queue wait
+ * behind one another's long batches.  Errors: PRAND_ERR_ARG, PRAND_ERR_NOMEM,
+ * PRAND_ERR_CUDA. */
 prand_status_t prand_server_create(prand_server_t *srv, uint64_t seed, uint64_t output_bytes,
                                    uint32_t slots_per_generator);
 /* Queue a request; *id identifies it.  Thread-safe.  Errors: PRAND_ERR_ARG. */

@@ -22,6 +22,7 @@
 #include <deque>
 #include <list>
 #include <map>
+#include <set>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -42,36 +43,60 @@ double now_s()
 size_t esz(int dtype) { return dtype == PRAND_DTYPE_F64 ? 8 : 4; }
 
 // First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
+// Output arena: best fit among the free blocks, found through a size-ordered
+// index (O(log n) per allocation however fragmented the arena is), and
+// neighbouring free blocks merged on release through the offset-ordered map.
 struct Arena {
-    std::map<uint64_t, uint64_t> free_;  // offset -> bytes
+    std::map<uint64_t, uint64_t> free_;         // offset -> bytes
+    std::set<std::pair<uint64_t, uint64_t>> by_size;  // (bytes, offset) of the same blocks
     uint64_t used = 0, top = 0;
-    explicit Arena(uint64_t cap = 0) { if (cap) free_[0] = cap; }
+    explicit Arena(uint64_t cap = 0)
+    {
+        if (cap) add(0, cap);
+    }
+    void add(uint64_t off, uint64_t bytes)
+    {
+        free_[off] = bytes;
+        by_size.emplace(bytes, off);
+    }
+    void drop(std::map<uint64_t, uint64_t>::iterator it)
+    {
+        by_size.erase({ it->second, it->first });
+        free_.erase(it);
+    }
     bool alloc(uint64_t bytes, uint64_t *off)
     {
         bytes = (bytes + 255) & ~255ull;
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= bytes) {
-                *off = it->first;
-                const uint64_t rest = it->second - bytes, roff = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[roff] = rest;
-                used += bytes;
-                top = std::max(top, roff);
-                return true;
-            }
-        return false;
+        auto fit = by_size.lower_bound({ bytes, 0 });
+        if (fit == by_size.end()) return false;
+        const uint64_t boff = fit->second, bsize = fit->first;
+        drop(free_.find(boff));
+        if (bsize > bytes) add(boff + bytes, bsize - bytes);
+        *off = boff;
+        used += bytes;
+        top = std::max(top, boff + bytes);
+        return true;
     }
     void release(uint64_t off, uint64_t bytes)
     {
         bytes = (bytes + 255) & ~255ull;
         used -= bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + bytes == nx->first) {  // merge with the block after
+            bytes += nx->second;
+            auto after = std::next(nx);
+            drop(nx);
+            nx = after;
         }
+        if (nx != free_.begin()) {  // and with the block before
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                off = pv->first;
+                bytes += pv->second;
+                drop(pv);
+            }
+        }
+        add(off, bytes);
     }
 };
 

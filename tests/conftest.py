@@ -3,6 +3,10 @@ import sys
 
 import pytest
 
+# The request server keeps 32 flights, each on its own stream: give them their
+# own hardware queues (read by CUDA when it starts, so set before any test runs).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
