@@ -51,9 +51,9 @@ SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per stream of one fill of 1024 outputs, from one ncu
 # capture of the current kernels at that shape (profiles/traffic_bulk_fill.md);
 # None for other shapes.
-TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.3217e9 / 2**18, "MT19937.f32": 2.3207e9 / 2**18,
-                           "LFSR113.u32": 1.0222e9 / 2**18, "LFSR113.f32": 1.0224e9 / 2**18,
-                           "GM61.u32": 1.2781e9 / 2**18, "GM61.f32": 1.2788e9 / 2**18}
+TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.3205e9 / 2**18, "MT19937.f32": 2.3185e9 / 2**18,
+                           "LFSR113.u32": 1.0263e9 / 2**18, "LFSR113.f32": 1.0264e9 / 2**18,
+                           "GM61.u32": 1.2774e9 / 2**18, "GM61.f32": 1.2790e9 / 2**18}
 # Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
