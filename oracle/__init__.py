@@ -62,6 +62,12 @@ def lib():
             L.orc_stream_range_v.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                              ctypes.c_uint64, vp]
             L.orc_variant.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), u64p]
+            L.orc_stream_spaced.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, vp]
+            L.orc_freq_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp]
+            L.orc_serial_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp]
+            L.orc_gap_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, vp]
+            for nm in ("orc_freq_counts", "orc_serial_counts", "orc_gap_counts"):
+                getattr(L, nm).restype = None
             for nm in ("orc_gen_u32", "orc_gen_f32", "orc_gen_f64"):
                 getattr(L, nm).argtypes = [ctypes.c_int, vp, vp, ctypes.c_uint64]
             for nm in ("orc_gen_many_u32", "orc_gen_many_f32", "orc_gen_many_f64"):
@@ -132,6 +138,14 @@ class State:
         st = cls(gen, seed)
         if lib().orc_stream_v(st.gen, ctypes.c_uint64(seed), variant, ctypes.c_uint64(k), st.buf):
             raise ValueError("no such stream variant")
+        return st
+
+    @classmethod
+    def spaced(cls, gen, seed: int, spacing_log2: int, k: int) -> "State":
+        """Stream k of the spaced layout: the base advanced by k * 2^spacing_log2."""
+        st = cls(gen, seed)
+        if lib().orc_stream_spaced(st.gen, ctypes.c_uint64(seed), spacing_log2, ctypes.c_uint64(k), st.buf):
+            raise ValueError("spacing out of range")
         return st
 
     def copy(self) -> "State":
@@ -240,3 +254,68 @@ def mt_apply_poly(st: State, poly: int) -> State:
         arr[i] = (poly >> (64 * i)) & 0xFFFFFFFFFFFFFFFF
     lib().orc_mt_apply_poly(st.buf, arr)
     return st
+
+
+# ---------------------------------------------------------------- tests
+# Spaced streams and the classical tests of the skip-ahead study (Table 3):
+# the oracle computes cell counts plainly; the chi-square tail comes from
+# scipy (a library routine).
+
+def spaced_outputs(gen, seed: int, spacing_log2: int, first: int, n: int, n_per: int = 1) -> np.ndarray:
+    """Outputs 0..n_per-1 of streams first..first+n-1 of the spaced layout
+    (stream k = base advanced by k * 2^spacing_log2), stream-major; with
+    n_per = 1 this is the subsequence u[(first + j) * 2^spacing_log2]."""
+    base = State.spaced(gen, seed, spacing_log2, first)
+    out = np.empty((n, n_per), dtype=np.uint32)
+    for j in range(n):
+        if j:
+            base.jump(1 << spacing_log2)  # stream first + j
+        out[j] = base.copy().u32(n_per)
+    return out
+
+
+def freq_counts(u: np.ndarray, bits: int) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    c = np.zeros(1 << bits, dtype=np.uint64)
+    lib().orc_freq_counts(u.ctypes.data, ctypes.c_uint64(u.size), bits, c.ctypes.data)
+    return c
+
+
+def serial_counts(u: np.ndarray, bits: int) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    c = np.zeros(1 << (2 * bits), dtype=np.uint64)
+    lib().orc_serial_counts(u.ctypes.data, ctypes.c_uint64(u.size), bits, c.ctypes.data)
+    return c
+
+
+def gap_counts(u: np.ndarray, lo: int, hi: int, t: int) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    c = np.zeros(t + 1, dtype=np.uint64)
+    lib().orc_gap_counts(u.ctypes.data, ctypes.c_uint64(u.size), ctypes.c_uint32(lo), ctypes.c_uint32(hi), t,
+                         c.ctypes.data)
+    return c
+
+
+def expected_counts(kind: str, n: int, counts: np.ndarray, bits: int = 0, lo: int = 0, hi: int = 0,
+                    t: int = 0) -> np.ndarray:
+    """Cell expectations under the uniform hypothesis (Knuth, Sec. 3.3.2):
+    frequency n / 2^b; serial floor(n / 2) / 4^b; gap G p (1-p)^r for r < t
+    and G (1-p)^t for the last cell, G = the number of gaps, p = (hi-lo)/2^32."""
+    if kind == "frequency":
+        return np.full(1 << bits, n / (1 << bits))
+    if kind == "serial":
+        return np.full(1 << (2 * bits), (n // 2) / (1 << (2 * bits)))
+    p = (hi - lo) / 2.0**32
+    G = float(counts.sum())
+    e = np.array([G * p * (1 - p) ** r for r in range(t)] + [G * (1 - p) ** t])
+    return e
+
+
+def chi2_test(kind: str, n: int, counts: np.ndarray, **kw):
+    """Pearson's statistic sum (O - E)^2 / E over the cells and its upper tail
+    probability with (cells - 1) degrees of freedom."""
+    from scipy.stats import chi2 as _chi2
+    e = expected_counts(kind, n, counts, **kw)
+    o = counts.astype(np.float64)
+    stat = float(((o - e) ** 2 / e).sum())
+    return stat, float(_chi2.sf(stat, len(e) - 1))

@@ -38,6 +38,17 @@
  *             GM/GQ ensemble of a variant spaces its points by that variant's
  *             N_max L (reading); LFSR113 long: L = 2^80 (reading: >= 1e24).
  *
+ *   Spaced    Table 3 tests the generators on the subsequence that skips
+ *             2^n values at each step; orc_stream_spaced() gives stream k of
+ *             the layout whose streams start k * 2^n outputs after the base,
+ *             so output 0 of streams 0, 1, 2, ... is that subsequence.
+ *   Tests     The statistical tests applied to such subsequences (the
+ *             paper runs TestU01; this build carries three classical tests
+ *             from Knuth, TAOCP vol. 2, Sec. 3.3.2): frequency (cells of the
+ *             top b bits), serial (non-overlapping pairs, cells of the top b
+ *             bits of each word), gap (Algorithm G's gap lengths for a word
+ *             range [lo, hi)).  The oracle computes the cell counts.
+ *
  * Parity unpinned (readings of gaps in the paper, pinned only by invariants):
  *   the GM/GQ output map, ensemble size, seeding and block lengths; the MRG32K3A
  *   output map and default state; the LFSR113 default state and combination;
@@ -834,6 +845,63 @@ int orc_stream_range_v(int gen, uint64_t seed, int v, uint64_t first, uint64_t n
 int orc_stream_range(int gen, uint64_t seed, uint64_t first, uint64_t n, void *out)
 {
     return orc_stream_range_v(gen, seed, 0, first, n, out);
+}
+
+/* Stream k of the spaced layout (Table 3's skip-ahead of 2^sp values): the
+ * seeded state of the default variant advanced by k * 2^sp. */
+int orc_stream_spaced(int gen, uint64_t seed, uint32_t sp, uint64_t k, void *st)
+{
+    if (sp + 64 > 64 * NBIG) return -1;
+    uint64_t e[NBIG];
+    memset(e, 0, sizeof e);
+    /* e = k << sp, a 512-bit number */
+    const int w = (int)(sp / 64), b = (int)(sp % 64);
+    e[w] = k << b;
+    if (b && w + 1 < NBIG) e[w + 1] = k >> (64 - b);
+    if (is_gm(gen)) gm_seed_v(gen, 0, st, seed);
+    else if (orc_seed(gen, seed, st)) return -1;
+    return orc_jump(gen, st, e);
+}
+
+/* ------------------------------------------------------------------ */
+/* Statistical tests (Knuth, TAOCP vol. 2, Sec. 3.3.2): cell counts.   */
+/* ------------------------------------------------------------------ */
+
+/* Frequency test: the top b bits of each word select one of 2^b cells. */
+void orc_freq_counts(const uint32_t *u, uint64_t n, int b, uint64_t *cnt)
+{
+    memset(cnt, 0, sizeof(uint64_t) << b);
+    for (uint64_t i = 0; i < n; ++i) cnt[u[i] >> (32 - b)] += 1;
+}
+
+/* Serial test on non-overlapping pairs (u[2i], u[2i+1]), i < n/2: the cell is
+ * (top b bits of u[2i]) * 2^b + (top b bits of u[2i+1]). */
+void orc_serial_counts(const uint32_t *u, uint64_t n, int b, uint64_t *cnt)
+{
+    memset(cnt, 0, sizeof(uint64_t) << (2 * b));
+    for (uint64_t i = 0; i + 1 < n; i += 2) {
+        const uint64_t a = u[i] >> (32 - b), c = u[i + 1] >> (32 - b);
+        cnt[(a << b) | c] += 1;
+    }
+}
+
+/* Gap test: word u is a hit when lo <= u < hi.  Walking the words in order,
+ * every hit closes a gap whose length r is the number of non-hits since the
+ * previous hit (for the first hit: since the start of the sequence).  Gaps of
+ * length r < t go to cell r, longer ones to cell t; the non-hits after the
+ * last hit close no gap. */
+void orc_gap_counts(const uint32_t *u, uint64_t n, uint32_t lo, uint32_t hi, int t, uint64_t *cnt)
+{
+    memset(cnt, 0, sizeof(uint64_t) * (size_t)(t + 1));
+    uint64_t r = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (u[i] >= lo && u[i] < hi) {
+            cnt[r < (uint64_t)t ? r : (uint64_t)t] += 1;
+            r = 0;
+        } else {
+            r += 1;
+        }
+    }
 }
 
 void orc_gen_u32(int gen, void *st, uint32_t *out, uint64_t n)
