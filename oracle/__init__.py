@@ -65,7 +65,7 @@ def lib():
             L.orc_stream_spaced.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, vp]
             L.orc_freq_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp]
             L.orc_serial_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, vp]
-            L.orc_gap_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, vp]
+            L.orc_gap_counts.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, vp]
             for nm in ("orc_freq_counts", "orc_serial_counts", "orc_gap_counts"):
                 getattr(L, nm).restype = None
             for nm in ("orc_gen_u32", "orc_gen_f32", "orc_gen_f64"):
@@ -291,7 +291,7 @@ def serial_counts(u: np.ndarray, bits: int) -> np.ndarray:
 def gap_counts(u: np.ndarray, lo: int, hi: int, t: int) -> np.ndarray:
     u = np.ascontiguousarray(u, dtype=np.uint32)
     c = np.zeros(t + 1, dtype=np.uint64)
-    lib().orc_gap_counts(u.ctypes.data, ctypes.c_uint64(u.size), ctypes.c_uint32(lo), ctypes.c_uint32(hi), t,
+    lib().orc_gap_counts(u.ctypes.data, ctypes.c_uint64(u.size), ctypes.c_uint64(lo), ctypes.c_uint64(hi), t,
                          c.ctypes.data)
     return c
 

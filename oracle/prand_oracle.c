@@ -885,17 +885,18 @@ void orc_serial_counts(const uint32_t *u, uint64_t n, int b, uint64_t *cnt)
     }
 }
 
-/* Gap test: word u is a hit when lo <= u < hi.  Walking the words in order,
+/* Gap test: word u is a hit when lo <= u < hi (hi <= 2^32, so the range may
+ * run to the top word).  Walking the words in order,
  * every hit closes a gap whose length r is the number of non-hits since the
  * previous hit (for the first hit: since the start of the sequence).  Gaps of
  * length r < t go to cell r, longer ones to cell t; the non-hits after the
  * last hit close no gap. */
-void orc_gap_counts(const uint32_t *u, uint64_t n, uint32_t lo, uint32_t hi, int t, uint64_t *cnt)
+void orc_gap_counts(const uint32_t *u, uint64_t n, uint64_t lo, uint64_t hi, int t, uint64_t *cnt)
 {
     memset(cnt, 0, sizeof(uint64_t) * (size_t)(t + 1));
     uint64_t r = 0;
     for (uint64_t i = 0; i < n; ++i) {
-        if (u[i] >= lo && u[i] < hi) {
+        if ((uint64_t)u[i] >= lo && (uint64_t)u[i] < hi) {
             cnt[r < (uint64_t)t ? r : (uint64_t)t] += 1;
             r = 0;
         } else {

@@ -83,6 +83,12 @@ def test_gap_counts_invariants():
     lo, hi = 1 << 30, 3 << 30
     c = O.gap_counts(u, lo, hi, 10)
     assert int(c.sum()) == int(((u >= lo) & (u < hi)).sum())  # one gap per hit
+    # the hit range may run to the top word: [0, 2^32) hits every word, so every gap is 0;
+    # [2^32 - 1, 2^32) hits only the top word
+    c = O.gap_counts(u, 0, 1 << 32, 3)
+    assert c.tolist() == [u.size, 0, 0, 0]
+    w = np.array([5, 0xFFFFFFFF, 7, 7, 0xFFFFFFFF], dtype=np.uint32)
+    assert O.gap_counts(w, (1 << 32) - 1, 1 << 32, 3).tolist() == [0, 1, 1, 0]
     # hits exactly every m-th word: every gap but the first has length m - 1
     m = 4
     v = np.zeros(400, dtype=np.uint32)
