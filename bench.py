@@ -327,10 +327,12 @@ def run_gpu(args):
     del U, F
     torch.cuda.empty_cache()
 
-    table = single = None
+    table = single = study = None
     if not args.no_table and rank == 0:
         table = run_table(P, torch, sp, args)
         single = run_single(P, torch, sp, args)
+    if not args.no_study and rank == 0:
+        study = run_skipahead(P, torch, sp, args)
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(P, torch, sp, args)
@@ -357,6 +359,7 @@ def run_gpu(args):
             "e2e": e2e,
             "table": table,
             "single_stream": single,
+            "skipahead_study": study,
             "batched": batched,
             "serving": serving,
         }
@@ -420,6 +423,72 @@ def run_table(P, torch, sp, args):
     torch.cuda.empty_cache()
     return {"workload": "11 generators x 2^16 streams x 2^12 outputs (u32, then f32), seed 12345",
             "generators": out}
+
+
+def run_skipahead(P, torch, sp, args):
+    """The skip-ahead study of Table 3 on the GPU: for each generator the
+    subsequence skipping 2^n values per step (n = the largest of the paper's
+    rows) is output 0 of streams spaced 2^n apart; the frequency, serial and gap
+    tests give p-values (the paper counts p outside [1e-3, 1 - 1e-3] as
+    suspicious).  Times: spaced initialisation (the jumps) and generation,
+    wall clock with a synchronize; the three count launches, CUDA events.  Then
+    the count kernels alone over 2^30 words (4 GiB >> L2), against the HBM
+    roofline: 4 bytes read per word."""
+    hbm_peak, _ = _peaks()
+    stream = torch.cuda.current_stream()
+    kinds = {"frequency": P.TEST_FREQUENCY, "serial": P.TEST_SERIAL, "gap": P.TEST_GAP}
+    tests = [(name, P.make_test(kinds[name], **kw)) for name, kw in W.STUDY_TESTS]
+    cnt = torch.empty(4096, dtype=torch.int64, device="cuda")
+    res, suspicious = {}, 0
+    for g, n_skip in W.STUDY_SKIPS.items():
+        N = W.STUDY_WORDS_MT if g == "MT19937" else W.STUDY_WORDS
+        w = torch.empty(N, dtype=torch.int32, device="cuda")
+        h = P.prand_create(g, W.STUDY_SEED)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.prand_init_streams_spaced(h, n_skip, 0, N)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        P.prand_generate_u32(h, w.data_ptr(), 1, sp)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        P.prand_destroy(h)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pv, counts = {}, []
+        a.record(stream)
+        for name, t in tests:
+            c = cnt[:P.prand_test_cells(t)]
+            P.prand_test_counts(t, w.data_ptr(), N, c.data_ptr(), sp)
+            counts.append(c.clone())
+        b.record(stream)
+        torch.cuda.synchronize()
+        for (name, t), c in zip(tests, counts):
+            _, _, p = P.prand_test_evaluate(t, N, c.cpu().numpy().view("uint64").tolist())
+            pv[name] = p
+            suspicious += not (1e-3 <= p <= 1 - 1e-3)
+        res[g] = {"skip_log2": n_skip, "words": N, "p": pv, "init_ms": 1e3 * (t1 - t0),
+                  "generate_ms": 1e3 * (t2 - t1), "tests_ms": a.elapsed_time(b)}
+        del w
+    # count kernels alone on 2^30 words
+    n = 1 << 30
+    big = torch.empty(n, dtype=torch.int32, device="cuda")
+    h = P.prand_create("LFSR113", 5)
+    P.prand_init_streams(h, 0, 1 << 20)
+    P.prand_generate_u32(h, big.data_ptr(), n >> 20, sp)
+    P.prand_destroy(h)
+    kern = {}
+    for name, t in tests:
+        c = cnt[:P.prand_test_cells(t)]
+        ms = _time_calls(torch, stream, lambda: P.prand_test_counts(t, big.data_ptr(), n, c.data_ptr(), sp),
+                         warmup=3, reps=5)
+        gbs = 4.0 * n / (ms * 1e-3) / 1e9
+        kern[name] = {"ms": ms, "gb_per_s": gbs, "hbm_frac": gbs / hbm_peak}
+    del big, cnt
+    torch.cuda.empty_cache()
+    return {"workload": "Table 3 skip-ahead study: output 0 of 2^22 streams spaced 2^n apart (MT19937 2^20), "
+                        "frequency 2^10 cells, serial 2^5 x 2^5, gap [0, 2^29) t = 48; seed 20140401",
+            "generators": res, "p_outside_1e-3": suspicious, "tests_run": 3 * len(res),
+            "count_kernels_2^30_words": kern}
 
 
 def run_single(P, torch, sp, args):
@@ -532,6 +601,7 @@ def main():
     ap.add_argument("--no-per-request", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-table", action="store_true")
+    ap.add_argument("--no-study", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=5e4)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -118,6 +118,19 @@ prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint6
 prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uint64_t first_stream,
                                           uint64_t n_streams);
 
+/* Streams spaced 2^log2_spacing outputs apart: stream k = the base advanced by
+ * k * 2^log2_spacing (for GM/GQ the default variant's base ensemble).  This is
+ * the layout of the paper's skip-ahead study (Sec. 4, Table 3): output 0 of
+ * streams 0, 1, 2, ... is the subsequence that skips 2^n values at each step,
+ * and output i of them is the same subsequence started i values later.
+ * log2_spacing <= 448 for MT19937 and <= 127 for the other generators.  No
+ * capacity warning: streams overlap once more than 2^log2_spacing outputs are
+ * drawn from one, which the caller controls.  Generation, skip-ahead and
+ * checkpoints work as after prand_init_streams.
+ * Errors: as prand_init_streams, and PRAND_ERR_ARG for a spacing out of range. */
+prand_status_t prand_init_streams_spaced(prand_handle_t h, uint32_t log2_spacing, uint64_t first_stream,
+                                         uint64_t n_streams);
+
 /* Write the next n_per_stream outputs of every stream, stream-major:
  * dev_out[j * n_per_stream + i] = output i of stream j (rng_generate_gpu_array_,
  * Sec. 6).  Each stream continues where the previous generate call on the
@@ -325,6 +338,65 @@ prand_status_t prand_server_destroy(prand_server_t srv);
  * latency; *wall_s = time until the last completion. */
 prand_status_t prand_server_replay(prand_server_t srv, const prand_request_t *reqs, const double *arrival_s, size_t n,
                                    double *latency_s, double *wall_s);
+
+/* Statistical tests of generated words (the paper tests the generators and
+ * their skip-ahead subsequences with TestU01, Secs. 3-4, Tables 1 and 3; these are
+ * three classical tests from Knuth, TAOCP vol. 2, Sec. 3.3.2):
+ *   PRAND_TEST_FREQUENCY  the top `bits` bits of each word select one of
+ *                         2^bits cells (1 <= bits <= 12);
+ *   PRAND_TEST_SERIAL     non-overlapping pairs (u[2i], u[2i+1]), i < n/2; the
+ *                         cell is (top bits of u[2i]) * 2^bits + (top bits of
+ *                         u[2i+1]) (1 <= bits <= 6, 4^bits cells; an odd last
+ *                         word is not used);
+ *   PRAND_TEST_GAP        u is a hit when lo <= u < hi (lo < hi <= 2^32); each
+ *                         hit closes a gap of r non-hits since the previous hit
+ *                         (for the first hit, since word 0); cell r counts gaps
+ *                         of length r < t, cell t those of length >= t
+ *                         (1 <= t <= 1024); words after the last hit close none. */
+#define PRAND_TEST_FREQUENCY 0
+#define PRAND_TEST_SERIAL 1
+#define PRAND_TEST_GAP 2
+typedef struct {
+    int32_t kind;   /* PRAND_TEST_* */
+    uint32_t bits;  /* frequency, serial */
+    uint32_t t;     /* gap */
+    uint32_t pad;
+    uint64_t lo;    /* gap */
+    uint64_t hi;    /* gap */
+} prand_test_t;
+
+/* Number of cells of a test, or 0 if its parameters are out of range. */
+uint32_t prand_test_cells(const prand_test_t *test);
+
+/* The cells' counts over dev_words[0..n): dev_counts (caller-owned device
+ * memory, prand_test_cells() uint64 entries, 8-byte aligned) is overwritten.
+ * dev_words: n words in device memory, 4-byte aligned (16-byte alignment gives
+ * vector loads).  n < 2^40.  Asynchronous on `stream`; the gap test takes
+ * stream-ordered scratch (cudaMallocAsync) of 16 bytes per 2^14 words.
+ * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
+prand_status_t prand_test_counts(const prand_test_t *test, const uint32_t *dev_words, uint64_t n,
+                                 uint64_t *dev_counts, prand_stream_t stream);
+
+/* Pearson's chi-square statistic of host_counts (the counts of `test` over n
+ * words) against the cells' expectations under the uniform hypothesis, and
+ * its upper tail probability with (cells - 1) degrees of freedom:
+ *   frequency  n / 2^bits per cell;
+ *   serial     floor(n / 2) / 4^bits per cell;
+ *   gap        G p (1 - p)^r for r < t and G (1 - p)^t, G = the number of
+ *              gaps (the counts' sum), p = (hi - lo) / 2^32.
+ * The tail probability is that of the chi-square law, valid when every
+ * expectation is large (say >= 5); a p-value outside [1e-3, 1 - 1e-3] is the
+ * paper's threshold for a suspicious result (Secs. 3-4).  Any output pointer may
+ * be NULL.  Errors: PRAND_ERR_ARG (invalid test, n too small for one cell). */
+prand_status_t prand_test_evaluate(const prand_test_t *test, uint64_t n, const uint64_t *host_counts, double *chi2,
+                                   double *dof, double *pvalue);
+
+/* Upper tail probability of the chi-square law with dof degrees of freedom at
+ * x (x >= 0, dof > 0): the regularized incomplete gamma function Q(dof/2, x/2),
+ * by its power series below x/2 < dof/2 + 1 and its continued fraction above
+ * (evaluated by the modified Lentz method).  Returns NaN for invalid
+ * arguments. */
+double prand_chi2_sf(double x, double dof);
 
 /* No counterpart in the paper.  MRG32K3A u32 generation that allocates no
  * memory, for callers that cannot call cudaMalloc: code that owns all device

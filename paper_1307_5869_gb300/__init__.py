@@ -39,7 +39,8 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_server_query", "prand_server_read", "prand_server_completed", "prand_server_release", "prand_server_stats",
            "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
            "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
-           "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2"]
+           "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2", "prand_init_streams_spaced",
+           "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf"]
 
 
 class PrandError(RuntimeError):
@@ -59,6 +60,14 @@ class Request(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_int32), ("dtype", ctypes.c_int32), ("stream", ctypes.c_uint64),
                 ("length", ctypes.c_uint64), ("dev_out", ctypes.c_void_p)]
 
+
+class Test(ctypes.Structure):
+    """prand_test_t: kind (TEST_*), bits (frequency, serial), t, lo, hi (gap)."""
+    _fields_ = [("kind", ctypes.c_int32), ("bits", ctypes.c_uint32), ("t", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+
+TEST_FREQUENCY, TEST_SERIAL, TEST_GAP = 0, 1, 2
 
 _lib = None
 
@@ -80,6 +89,14 @@ def load(build_if_missing: bool = False):
     L.prand_init_streams.argtypes = [H, u64, u64]
     L.prand_init_streams_variant.argtypes = [H, ctypes.c_int32, u64, u64]
     L.prand_skipahead_pow2.argtypes = [H, u64, ctypes.c_uint32]
+    L.prand_init_streams_spaced.argtypes = [H, ctypes.c_uint32, u64, u64]
+    L.prand_test_cells.argtypes = [ctypes.POINTER(Test)]
+    L.prand_test_cells.restype = ctypes.c_uint32
+    L.prand_test_counts.argtypes = [ctypes.POINTER(Test), ctypes.c_void_p, u64, ctypes.c_void_p, ctypes.c_void_p]
+    L.prand_test_evaluate.argtypes = [ctypes.POINTER(Test), u64, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.prand_chi2_sf.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.prand_chi2_sf.restype = ctypes.c_double
     for nm in ("prand_generate_u32", "prand_generate_f32", "prand_generate_f64", "prand_generate_host_u32",
                "prand_generate_host_f32", "prand_generate_host_f64"):
         getattr(L, nm).argtypes = [H, ctypes.c_void_p, u64, ctypes.c_void_p]
@@ -119,7 +136,8 @@ def load(build_if_missing: bool = False):
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_float)]
     for nm in EXPORTS:
-        if nm not in ("prand_status_string", "prand_kernel_launches", "prand_device_state_bytes"):
+        if nm not in ("prand_status_string", "prand_kernel_launches", "prand_device_state_bytes", "prand_test_cells",
+                      "prand_chi2_sf"):
             getattr(L, nm).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,6 +312,38 @@ def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out:
 
 
 MAP_MRG_F64 = 3
+
+
+def prand_init_streams_spaced(h: int, log2_spacing: int, first: int, n: int) -> None:
+    """Streams first..first+n-1 spaced 2^log2_spacing outputs apart (Table 3's layout)."""
+    _check(load().prand_init_streams_spaced(h, log2_spacing, first, n), "prand_init_streams_spaced")
+
+
+def make_test(kind: int, bits: int = 0, lo: int = 0, hi: int = 0, t: int = 0) -> Test:
+    return Test(kind, bits, t, 0, lo, hi)
+
+
+def prand_test_cells(test: Test) -> int:
+    return int(load().prand_test_cells(ctypes.byref(test)))
+
+
+def prand_test_counts(test: Test, dev_words: int, n: int, dev_counts: int, stream: int = 0) -> None:
+    """Cell counts of `test` over n device words into dev_counts (uint64, prand_test_cells entries)."""
+    _check(load().prand_test_counts(ctypes.byref(test), dev_words, n, dev_counts, stream), "prand_test_counts")
+
+
+def prand_test_evaluate(test: Test, n: int, counts) -> tuple:
+    """(chi2, degrees of freedom, p-value) of host counts (a sequence of ints) of `test` over n words."""
+    cells = prand_test_cells(test)
+    arr = (ctypes.c_uint64 * cells)(*[int(c) for c in counts])
+    chi2, dof, p = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().prand_test_evaluate(ctypes.byref(test), n, arr, ctypes.byref(chi2), ctypes.byref(dof),
+                                      ctypes.byref(p)), "prand_test_evaluate")
+    return chi2.value, dof.value, p.value
+
+
+def prand_chi2_sf(x: float, dof: float) -> float:
+    return float(load().prand_chi2_sf(x, dof))
 
 
 def prand_convert(dev_in: int, n: int, map_: int, dev_out: int, stream: int = 0) -> None:

@@ -62,8 +62,11 @@ bool variant_params(int gen, int v, Variant *out)
         if (v == 0) { nm = 3800000000000000000ull; L = (u128)1 << 34; }
         else if (v == 2) { nm = 4000000000ull; L = (u128)1 << 80; }
         break;
-    case PRAND_MRG32K3A: case PRAND_MT19937:
-        if (v == 0) nm = 10000000000000000000ull;  // L = 2^127 / 2^432, applied as shifts
+    case PRAND_MRG32K3A:
+        if (v == 0) { nm = 10000000000000000000ull; L = (u128)1 << kMrgStreamShift; }
+        break;
+    case PRAND_MT19937:
+        if (v == 0) nm = 10000000000000000000ull;  // L = 2^432 (above 128 bits): applied as a shift
         break;
     default: break;
     }
@@ -74,6 +77,25 @@ bool variant_params(int gen, int v, Variant *out)
     const u128 D = L * nm;  // below 2^117 for every GM/GQ variant
     out->D[0] = is_gm(gen) ? (uint64_t)D : 0;
     out->D[1] = is_gm(gen) ? (uint64_t)(D >> 64) : 0;
+    return true;
+}
+
+// Handle layouts: a Table 4 variant (0, 1, 2), or streams spaced 2^s apart
+// (kSpacedTag + s; the skip-ahead layout of Table 3).  The GM/GQ base of a
+// spaced layout is the default variant's ensemble.
+constexpr int32_t kSpacedTag = 0x10000;
+constexpr int kMaxSpacing = 127, kMaxSpacingMt = kMtPolyCount - 64;
+
+static bool layout_params(int gen, int32_t layout, Variant *V, int *mt_shift)
+{
+    *mt_shift = kMtStreamShift;
+    if (layout < kSpacedTag) return variant_params(gen, layout, V);
+    const int sp = layout - kSpacedTag;
+    if (sp > (gen == PRAND_MT19937 ? kMaxSpacingMt : kMaxSpacing) || !variant_params(gen, 0, V)) return false;
+    V->L[0] = sp < 64 ? 1ull << sp : 0;
+    V->L[1] = sp >= 64 ? 1ull << (sp - 64) : 0;
+    V->nmax = UINT64_MAX;  // a chosen spacing has no Table 4 capacity
+    *mt_shift = sp;
     return true;
 }
 
@@ -370,22 +392,24 @@ prand_status_t prand_create(prand_handle_t *out, prand_gen_t gen, uint64_t seed)
     return PRAND_OK;
 }
 
-prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uint64_t first_stream, uint64_t n_streams)
+static prand_status_t init_layout(prand_handle_t h, int32_t layout, uint64_t first_stream, uint64_t n_streams)
 {
     if (!h || n_streams == 0) return PRAND_ERR_ARG;
     Variant V;
-    if (!variant_params(h->gen, variant, &V)) return PRAND_ERR_ARG;
+    int mt_shift;
+    if (!layout_params(h->gen, layout, &V, &mt_shift)) return PRAND_ERR_ARG;
     uint64_t last;
     if (__builtin_add_overflow(first_stream, n_streams - 1, &last)) return PRAND_ERR_ARG;
     prand_status_t s = check_device(h);
     if (s != PRAND_OK) return s;
     if ((s = sync_last(h)) != PRAND_OK) return s;
-    if (is_gm(h->gen) && variant != h->base_variant) {
+    const int base_variant = layout < kSpacedTag ? layout : 0;
+    if (is_gm(h->gen) && base_variant != h->base_variant) {
         // the GM/GQ ensemble is spaced for its variant: seed the base again
         if ((s = gm_seed(h->gen, h->T, h->seed, V, h->d_base, 0)) != PRAND_OK) return s;
-        h->base_variant = variant;
+        h->base_variant = base_variant;
     }
-    h->variant = variant;
+    h->variant = layout;
     free_states(h);
     uint64_t bytes;
     if (mul_overflows(n_streams, state_bytes_per_stream(h->gen), &bytes)) return PRAND_ERR_ARG;
@@ -395,7 +419,7 @@ prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uin
         free_states(h);
         return PRAND_ERR_NOMEM;
     }
-    if (h->gen == PRAND_MT19937) s = mt_init(h->T, h->d_base, h->d_state, first_stream, n_streams, 0);
+    if (h->gen == PRAND_MT19937) s = mt_init(h->T, h->d_base, h->d_state, first_stream, n_streams, 0, mt_shift);
     else if (is_gm(h->gen)) s = gm_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, V, 0);
     else s = mrg_lfsr_init(h->gen, h->T, h->d_base, h->d_state, first_stream, n_streams, V, 0);
     if (s == PRAND_OK && cudaStreamSynchronize(0) != cudaSuccess) s = PRAND_ERR_CUDA;
@@ -410,9 +434,22 @@ prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uin
     return PRAND_OK;
 }
 
+prand_status_t prand_init_streams_variant(prand_handle_t h, int32_t variant, uint64_t first_stream, uint64_t n_streams)
+{
+    if (variant < 0 || variant >= kSpacedTag) return PRAND_ERR_ARG;
+    return init_layout(h, variant, first_stream, n_streams);
+}
+
 prand_status_t prand_init_streams(prand_handle_t h, uint64_t first_stream, uint64_t n_streams)
 {
-    return prand_init_streams_variant(h, 0, first_stream, n_streams);
+    return init_layout(h, 0, first_stream, n_streams);
+}
+
+prand_status_t prand_init_streams_spaced(prand_handle_t h, uint32_t log2_spacing, uint64_t first_stream,
+                                         uint64_t n_streams)
+{
+    if (log2_spacing > (uint32_t)kMaxSpacingMt) return PRAND_ERR_ARG;
+    return init_layout(h, kSpacedTag + (int32_t)log2_spacing, first_stream, n_streams);
 }
 
 prand_status_t prand_generate_u32(prand_handle_t h, uint32_t *dev_out, uint64_t n_per_stream, prand_stream_t stream)
@@ -536,8 +573,9 @@ prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t by
     BlobHeader hd;
     memcpy(&hd, host_buf, sizeof hd);
     Variant V;
+    int mt_shift;
     if (hd.magic != kBlobMagic || hd.version != kBlobVersion || hd.gen != h->gen || hd.n == 0 ||
-        !variant_params(h->gen, hd.variant, &V))
+        !layout_params(h->gen, hd.variant, &V, &mt_shift))
         return PRAND_ERR_STATE;
     uint64_t sb;
     if (mul_overflows(hd.n, state_bytes_per_stream(h->gen), &sb) || sb != hd.state_bytes ||

@@ -43,15 +43,28 @@ __global__ void mrg_seed_kernel(uint32_t *base, uint64_t seed)
     for (int i = 0; i < 3; ++i) { base[i] = x[i]; base[3 + i] = y[i]; }
 }
 
-// Stream j = base advanced by (first + j) * 2^127.
-__global__ void mrg_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n)
+// k * L for a 64-bit k and a 128-bit L: the exact 192-bit product.
+__device__ __forceinline__ void mul_64x128(uint64_t k, uint64_t llo, uint64_t lhi, uint64_t e[3])
+{
+    e[0] = k * llo;
+    const uint64_t c0 = __umul64hi(k, llo);
+    e[1] = k * lhi + c0;
+    e[2] = __umul64hi(k, lhi) + (e[1] < c0 ? 1u : 0u);
+}
+
+// Stream j = base advanced by (first + j) * L, L of 128 bits (2^127 in the
+// Table 4 layout); the exponent of up to 192 bits is exact.
+__global__ void mrg_init_kernel(const uint32_t *tab, const uint32_t *base, uint32_t *state, uint64_t first, uint64_t n,
+                                uint64_t llo, uint64_t lhi)
 {
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     uint32_t x[3] = { base[0], base[1], base[2] }, y[3] = { base[3], base[4], base[5] };
-    uint64_t k = first + j;
-    for (int b = 0; b < 64; ++b)
-        if ((k >> b) & 1u) mrg_apply_bit(tab, kMrgStreamShift + b, x, y);
+    uint64_t e[3];
+    mul_64x128(first + j, llo, lhi, e);
+    for (int w = 0; w < 3; ++w)
+        for (int b = 0; e[w] && b < 64; ++b)
+            if ((e[w] >> b) & 1u) mrg_apply_bit(tab, 64 * w + b, x, y);
     for (int i = 0; i < 3; ++i) { state[i * n + j] = x[i]; state[(3 + i) * n + j] = y[i]; }
 }
 
@@ -177,12 +190,8 @@ __global__ void lfsr_init_kernel(const uint32_t *tab, const uint32_t *base, uint
     uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     uint32_t z[4] = { base[0], base[1], base[2], base[3] };
-    const uint64_t k = first + j;
     uint64_t e[3];
-    e[0] = k * llo;
-    const uint64_t c0 = __umul64hi(k, llo);
-    e[1] = k * lhi + c0;
-    e[2] = __umul64hi(k, lhi) + (e[1] < c0 ? 1u : 0u);
+    mul_64x128(first + j, llo, lhi, e);
     for (int w = 0; w < 3; ++w)
         for (int b = 0; e[w] && b < 64; ++b)
             if ((e[w] >> b) & 1u) lfsr_apply_bit(tab, 64 * w + b, z);
@@ -285,7 +294,8 @@ prand_status_t mrg_lfsr_init(int gen, const DevTables *T, const void *d_base, vo
 {
     const unsigned B = 128;
     if (gen == PRAND_MRG32K3A)
-        mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n);
+        mrg_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->mrg, (const uint32_t *)d_base, (uint32_t *)d_state, first, n,
+                                                      V.L[0], V.L[1]);
     else
         lfsr_init_kernel<<<grid_for(n, B), B, 0, st>>>(T->lfsr, (const uint32_t *)d_base, (uint32_t *)d_state, first, n,
                                                        V.L[0], V.L[1]);

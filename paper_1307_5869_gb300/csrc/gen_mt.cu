@@ -136,18 +136,20 @@ prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st)
     return launch_check();
 }
 
-// streams j = 0..n-1 := base advanced by (first + j) * 2^432: stream 0 by the
-// bits of first, then a doubling tree (stream 2^b + j from stream j by 2^(432+b)).
-prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st)
+// streams j = 0..n-1 := base advanced by (first + j) * 2^shift (2^432 in the
+// Table 4 layout): stream 0 by the bits of first, then a doubling tree
+// (stream 2^b + j from stream j by 2^(shift + b)).
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st,
+                       int shift)
 {
     uint32_t *state = (uint32_t *)d_state;
     if (cudaMemcpyAsync(state, d_base, kMtN * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return PRAND_ERR_CUDA;
     if (first) {
         MtBits e = {};
-        // first * 2^432: bits 432 .. 495
+        // first * 2^shift: bits shift .. shift + 63
         for (int b = 0; b < 64; ++b)
-            if ((first >> b) & 1u) e.w[(kMtStreamShift + b) >> 6] |= 1ull << ((kMtStreamShift + b) & 63);
+            if ((first >> b) & 1u) e.w[(shift + b) >> 6] |= 1ull << ((shift + b) & 63);
         mt_multi_kernel<<<1, 32 * kMtWarpsPerBlock, 0, st>>>(T->mt, state, 1, e, nullptr);
         prand_status_t s = launch_check();
         if (s != PRAND_OK) return s;
@@ -156,7 +158,7 @@ prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, ui
         uint64_t have = 1ull << b;
         uint64_t count = min(have, n - have);
         mt_level_kernel<<<grid_warps(count), 32 * kMtWarpsPerBlock, 0, st>>>(
-            T->mt + (size_t)(kMtStreamShift + b) * kMtPolyWords, state, have, count);
+            T->mt + (size_t)(shift + b) * kMtPolyWords, state, have, count);
         prand_status_t s = launch_check();
         if (s != PRAND_OK) return s;
     }

@@ -171,7 +171,10 @@ prand_status_t gm_skip(int gen, const DevTables *T, void *d_state, uint64_t n, c
 prand_status_t gm_gen(int gen, const DevTables *T, void *d_state, void *d_spare, StreamRange &R, void *out, int dtype,
                       uint64_t nper, cudaStream_t st);
 prand_status_t mt_seed(uint64_t seed, void *d_base, cudaStream_t st);
-prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st);
+// Streams first..first+n-1, stream k = base advanced by k * 2^shift (the
+// Table 4 block length 2^432 by default; shift + 63 < kMtPolyCount).
+prand_status_t mt_init(const DevTables *T, const void *d_base, void *d_state, uint64_t first, uint64_t n, cudaStream_t st,
+                       int shift = kMtStreamShift);
 prand_status_t mt_skip(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const U256 &off, cudaStream_t st);
 prand_status_t mt_skip512(const DevTables *T, void *d_state, uint64_t n, uint32_t *idx, const uint64_t off[8],
                           cudaStream_t st);

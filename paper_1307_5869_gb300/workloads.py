@@ -41,6 +41,18 @@ TABLE_SEED = 12345
 # One stream of MRG32K3A from the default state, 2^20 outputs.
 SINGLE_LENGTH = 1 << 20
 
+# Skip-ahead study (Table 3): per generator the largest n of the paper's rows
+# (2^n values skipped per step); the subsequence is output 0 of 2^22 streams
+# spaced 2^n apart (2^20 for MT19937, whose states are 2.5 KB), tested for
+# frequency (2^10 cells), serial pairs (2^10 cells) and gaps (hit range
+# [0, 2^29), p = 1/8, 49 cells).
+STUDY_SKIPS = {"GM19": 21, "GM29": 24, "GM31": 24, "GM55": 60, "GM61": 75, "GQ58_1": 24, "GQ58_3": 24,
+               "GQ58_4": 24, "LFSR113": 75, "MRG32K3A": 90, "MT19937": 440}
+STUDY_WORDS = 1 << 22
+STUDY_WORDS_MT = 1 << 20
+STUDY_SEED = 20140401
+STUDY_TESTS = (("frequency", dict(bits=10)), ("serial", dict(bits=5)), ("gap", dict(lo=0, hi=1 << 29, t=48)))
+
 
 def batched_requests(n: int = 10_000, seed: int = 7, max_log2: int = 20):
     """Requests (gen, stream, length, dtype=u32): generator uniform over the

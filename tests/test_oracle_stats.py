@@ -130,3 +130,14 @@ def test_tests_reject_a_biased_sequence_and_accept_a_generator():
                              ("gap", O.gap_counts(d, 0, 1 << 30, 12), dict(lo=0, hi=1 << 30, t=12))):
         _, p = O.chi2_test(kind, d.size, counts, **kw)
         assert 1e-4 < p < 1 - 1e-4, (kind, p)
+
+
+def test_gm19_skip_ahead_subsequence_period():
+    # GM19's period is p^2 - 1 = 2^20 (2^18 - 1) (Table 2, p = 2^19 - 1), so the
+    # subsequence that skips 2^21 values per step repeats after 2^18 - 1 values
+    p = (1 << 19) - 1
+    assert p * p - 1 == (1 << 20) * ((1 << 18) - 1)
+    a = O.spaced_outputs("GM19", 5, 21, 0, 4, 1)[:, 0]
+    b = O.spaced_outputs("GM19", 5, 21, (1 << 18) - 1, 4, 1)[:, 0]
+    c = O.spaced_outputs("GM19", 5, 21, 1 << 17, 4, 1)[:, 0]
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
