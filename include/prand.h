@@ -372,7 +372,7 @@ uint32_t prand_test_cells(const prand_test_t *test);
  * memory, prand_test_cells() uint64 entries, 8-byte aligned) is overwritten.
  * dev_words: n words in device memory, 4-byte aligned (16-byte alignment gives
  * vector loads).  n < 2^40.  Asynchronous on `stream`; the gap test takes
- * stream-ordered scratch (cudaMallocAsync) of 16 bytes per 2^14 words.
+ * stream-ordered scratch (cudaMallocAsync) of 16 bytes per 2^13 words.
  * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_NOMEM, PRAND_ERR_CUDA. */
 prand_status_t prand_test_counts(const prand_test_t *test, const uint32_t *dev_words, uint64_t n,
                                  uint64_t *dev_counts, prand_stream_t stream);

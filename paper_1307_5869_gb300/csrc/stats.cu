@@ -13,7 +13,7 @@ namespace prand {
 namespace {
 
 constexpr unsigned kBlock = 256;
-constexpr int kGapChunkLog = 14;  // words per gap chunk (one warp each)
+constexpr int kGapChunkLog = 13;  // words per gap chunk (one warp each)
 constexpr uint32_t kMaxGapT = 1024;
 constexpr unsigned kStitchThreads = 1024;
 
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlock) hist_kernel(const uint32_t *__restrict
 }
 
 // ------------------------------------------------------------------ gap
-// One warp per chunk of 2^14 words, read 32 consecutive words per round (one
+// One warp per chunk of 2^13 words, read 32 consecutive words per round (one
 // per lane).  The round's hits form a ballot mask in sequence order, so a
 // hit's predecessor is the highest set bit below its lane, or the last hit of
 // an earlier round.  Positions inside a chunk are 32-bit offsets, kept as
@@ -101,12 +101,22 @@ __global__ void __launch_bounds__(kBlock) hist_kernel(const uint32_t *__restrict
 // u - lo <= hi - lo - 1.  The first hit of a chunk needs the previous chunk's
 // last hit, so it is left to the stitch kernel: each chunk records its first
 // and last hit (absolute position + 1; 0 = no hit).
+// Shared-memory cells of a block: cells 0..t of the gap lengths, then one
+// dummy cell per lane.  Every lane adds 1 in every step -- to its gap's cell
+// when it closes a gap, else to its own dummy cell -- so the increment needs
+// neither a branch nor a predicate, and the dummies never collide.
+__device__ __forceinline__ void red_shared(uint32_t addr)
+{
+    asm volatile("red.shared.add.u32 [%0], 1;" :: "r"(addr));
+}
+
 template <bool FULL>
 __device__ __forceinline__ void gap_chunk(const uint32_t *__restrict__ u, uint32_t len, uint32_t lo, uint32_t span_m1,
-                                          uint32_t t, uint32_t *h, int lane, uint32_t &first1, uint32_t &prev1)
+                                          uint32_t t, uint32_t hs, int lane, uint32_t &first1, uint32_t &prev1)
 {
     constexpr int U = 8;  // rounds whose loads are issued together
     const unsigned below_mask = (1u << lane) - 1u;
+    const uint32_t dummy = hs + 4u * (t + 1 + lane);
     for (uint32_t r0 = 0; r0 < len; r0 += 32 * U) {
         uint32_t x[U];
 #pragma unroll
@@ -119,40 +129,82 @@ __device__ __forceinline__ void gap_chunk(const uint32_t *__restrict__ u, uint32
             const uint32_t r = r0 + 32 * k;
             const bool hit = (FULL || r + lane < len) && x[k] - lo <= span_m1;
             const unsigned m = __ballot_sync(kFull, hit);
-            if (m) {
-                if (hit) {
-                    const unsigned below = m & below_mask;
-                    const uint32_t p1 = below ? r + 32 - __clz(below) : prev1;
-                    if (p1) {
-                        const uint32_t g = r + lane - p1;
-                        atomicAdd(&h[min(g, t)], 1u);
-                    }
-                }
-                if (!first1) first1 = r + __ffs(m);
-                prev1 = r + 32 - __clz(m);
-            }
+            const unsigned below = m & below_mask;
+            const uint32_t p1 = below ? r + 32 - __clz(below) : prev1;
+            red_shared((hit && p1) ? hs + 4u * min(r + lane - p1, t) : dummy);
+            if (!prev1 && m) first1 = r + __ffs(m);  // warp-uniform: once per chunk
+            prev1 = m ? r + 32 - __clz(m) : prev1;
         }
     }
 }
 
+// The same for a whole chunk of 16-byte aligned words, four consecutive words
+// per lane and round (128 words): a lane's hits are walked in order, starting
+// from the last hit before its words -- the last hit of the nearest lower lane
+// that has one (ballot of "lane has a hit", one shuffle), or of an earlier
+// round.  One ballot per 128 words instead of one per 32.
+__device__ __forceinline__ void gap_chunk_vec(const uint32_t *__restrict__ u, uint32_t lo, uint32_t span_m1,
+                                              uint32_t t, uint32_t hs, int lane, uint32_t &first1, uint32_t &prev1)
+{
+    constexpr uint32_t C = 1u << kGapChunkLog;
+    constexpr int U = 4;  // rounds whose loads are issued together
+    const unsigned below_mask = (1u << lane) - 1u;
+    const uint32_t dummy = hs + 4u * (t + 1 + lane);
+    for (uint32_t r0 = 0; r0 < C; r0 += 128 * U) {
+        uint4 v[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) v[k] = *reinterpret_cast<const uint4 *>(u + r0 + 128 * k + 4 * lane);
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t b = r0 + 128 * k + 4 * lane;  // offset of this lane's first word
+            const bool h0 = v[k].x - lo <= span_m1, h1 = v[k].y - lo <= span_m1;
+            const bool h2 = v[k].z - lo <= span_m1, h3 = v[k].w - lo <= span_m1;
+            const uint32_t last = h3 ? b + 4 : h2 ? b + 3 : h1 ? b + 2 : h0 ? b + 1 : 0u;
+            const unsigned lm = __ballot_sync(kFull, last != 0u);
+            const unsigned below = lm & below_mask;
+            const uint32_t from = __shfl_sync(kFull, last, below ? 31 - __clz(below) : lane);
+            if (!prev1 && lm) {  // warp-uniform: the chunk's first hit, once per chunk
+                const uint32_t firsthere = h0 ? b + 1 : h1 ? b + 2 : h2 ? b + 3 : b + 4;
+                first1 = __shfl_sync(kFull, firsthere, __ffs(lm) - 1);
+            }
+            uint32_t p1 = below ? from : prev1;
+#define PRAND_GAP_WORD(H, J)                                                   \
+            red_shared(((H) && p1) ? hs + 4u * min(b + (J) - p1, t) : dummy);  \
+            p1 = (H) ? b + (J) + 1 : p1;
+            PRAND_GAP_WORD(h0, 0)
+            PRAND_GAP_WORD(h1, 1)
+            PRAND_GAP_WORD(h2, 2)
+            PRAND_GAP_WORD(h3, 3)
+#undef PRAND_GAP_WORD
+            prev1 = lm ? __reduce_max_sync(kFull, last) : prev1;
+        }
+    }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kBlock) gap_chunk_kernel(const uint32_t *__restrict__ u, uint64_t n, uint32_t lo,
                                                            uint32_t span_m1, uint32_t t, uint64_t nchunks,
                                                            unsigned long long *__restrict__ counts,
                                                            unsigned long long *__restrict__ first1,
                                                            unsigned long long *__restrict__ last1)
 {
-    __shared__ uint32_t h[kMaxGapT + 1];
-    for (uint32_t i = threadIdx.x; i <= t; i += blockDim.x) h[i] = 0;
+    __shared__ uint32_t h[kMaxGapT + 1 + 32];  // cells 0..t, then the lanes' dummy cells
+    for (uint32_t i = threadIdx.x; i <= t + 32; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const uint32_t hs = (uint32_t)__cvta_generic_to_shared(h);
     const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
     constexpr uint32_t C = 1u << kGapChunkLog;
     for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; c < nchunks; c += nwarps) {
         const uint64_t base = c << kGapChunkLog;
         const uint32_t len = (uint32_t)min((uint64_t)C, n - base);
         uint32_t f1 = 0, p1 = 0;
-        if (len == C) gap_chunk<true>(u + base, C, lo, span_m1, t, h, lane, f1, p1);
-        else gap_chunk<false>(u + base, len, lo, span_m1, t, h, lane, f1, p1);
+        if (len == C) {
+            if (VEC) gap_chunk_vec(u + base, lo, span_m1, t, hs, lane, f1, p1);
+            else gap_chunk<true>(u + base, C, lo, span_m1, t, hs, lane, f1, p1);
+        } else {
+            gap_chunk<false>(u + base, len, lo, span_m1, t, hs, lane, f1, p1);
+        }
         if (lane == 0) {
             first1[c] = f1 ? base + f1 : 0ull;
             last1[c] = p1 ? base + p1 : 0ull;
@@ -180,16 +232,25 @@ __global__ void __launch_bounds__(kStitchThreads) gap_stitch_kernel(const unsign
     const uint64_t c0 = min((uint64_t)threadIdx.x * per, nchunks), c1 = min(c0 + per, nchunks);
     __syncthreads();
     uint64_t mine = 0, prev = 0;  // this run's first hit, its latest hit (position + 1; 0 = none)
-    for (uint64_t c = c0; c < c1; ++c) {
-        const uint64_t f = first1[c];
-        if (!f) continue;
-        if (prev) {
-            const uint64_t g = f - prev - 1;
-            atomicAdd(&h[g < t ? (uint32_t)g : t], 1u);
-        } else {
-            mine = f;
+    constexpr int B = 8;          // records loaded together
+    for (uint64_t cb = c0; cb < c1; cb += B) {
+        uint64_t f[B], l[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            f[k] = cb + k < c1 ? first1[cb + k] : 0ull;
+            l[k] = cb + k < c1 ? last1[cb + k] : 0ull;
         }
-        prev = last1[c];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            if (!f[k]) continue;
+            if (prev) {
+                const uint64_t g = f[k] - prev - 1;
+                atomicAdd(&h[g < t ? (uint32_t)g : t], 1u);
+            } else {
+                mine = f[k];
+            }
+            prev = l[k];
+        }
     }
     scan[threadIdx.x] = prev;
     __syncthreads();
@@ -296,8 +357,13 @@ prand_status_t prand_test_counts(const prand_test_t *test, const uint32_t *dev_w
         return PRAND_ERR_NOMEM;
     }
     const unsigned grid = grid_for_words(nchunks * 32);
-    gap_chunk_kernel<<<grid, kBlock, 0, st>>>(dev_words, n, (uint32_t)test->lo, (uint32_t)(test->hi - test->lo - 1),
-                                             test->t, nchunks, cnt, rec, rec + nchunks);
+    const uint32_t lo = (uint32_t)test->lo, span_m1 = (uint32_t)(test->hi - test->lo - 1);
+    if ((uintptr_t)dev_words % 16 == 0)
+        gap_chunk_kernel<true><<<grid, kBlock, 0, st>>>(dev_words, n, lo, span_m1, test->t, nchunks, cnt, rec,
+                                                        rec + nchunks);
+    else
+        gap_chunk_kernel<false><<<grid, kBlock, 0, st>>>(dev_words, n, lo, span_m1, test->t, nchunks, cnt, rec,
+                                                         rec + nchunks);
     prand_status_t s = launch_check();
     if (s == PRAND_OK) {
         gap_stitch_kernel<<<1, kStitchThreads, 0, st>>>(rec, rec + nchunks, nchunks, test->t, cnt);

@@ -10,7 +10,7 @@ import paper_1307_5869_gb300 as P  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-CHUNK = 1 << 14  # words per gap chunk on the GPU
+CHUNK = 1 << 13  # words per gap chunk on the GPU
 
 
 def _gen(h, n, m):
