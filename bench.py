@@ -151,6 +151,37 @@ def oracle_rates(budget_s: float = 6.0, streams: int = 4):
     return rates, detail
 
 
+def _oracle_worker(job):
+    """One process of the all-cores timing: the oracle on its own streams."""
+    gen, first, streams, budget_s = job
+    import oracle as O
+    st = O.Streams(gen, W.bulk_seed(0), first, streams)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        st.generate("u32", W.BULK_PER_STREAM)
+        st.generate("f32", W.BULK_PER_STREAM)
+        n += 2 * streams * W.BULK_PER_STREAM
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return n, time.perf_counter() - t0
+
+
+def oracle_rates_all_cores(budget_s: float = 6.0, streams: int = 4):
+    """The same timing with one oracle process per host core (a spawn pool,
+    as the process already uses CUDA), each on its own streams; the rate is
+    the sum over the processes."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    share = {"MT19937": 0.2, "LFSR113": 0.2, "GM61": 0.6}
+    rates = {}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for gen in W.BULK_GENERATORS:
+            jobs = [(gen, k * streams, streams, budget_s * share[gen]) for k in range(cores)]
+            rates[gen] = sum(n / dt for n, dt in pool.map(_oracle_worker, jobs))
+    return rates, cores
+
+
 def mix_throughput(rates: dict) -> float:
     """Whole-workload samples/s for equal sample counts per generator."""
     per = 2 * W.BULK_STREAMS * W.BULK_PER_STREAM
@@ -372,6 +403,12 @@ def run_gpu(args):
                 "sample": f"first 4 streams of each generator, u32+f32 rounds of 2^10 outputs, "
                           f"~{args.cpu_budget:.0f} s of single-thread oracle time, extrapolated to the mix",
                 "per_generator_samples_per_s": rates, "detail": detail}
+            all_rates, cores = oracle_rates_all_cores(budget_s=args.cpu_budget)
+            line["cpu_baseline"]["all_cores"] = {
+                "value": mix_throughput(all_rates) / 1e9, "unit": UNIT, "cores": cores,
+                "sample": f"one oracle process per core, each on 4 streams of its own, "
+                          f"~{args.cpu_budget:.0f} s, extrapolated to the mix",
+                "per_generator_samples_per_s": all_rates}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
