@@ -350,7 +350,8 @@ def run_gpu(args):
         e2e = {"value": world * samples_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(gens) * nS * nP * 8,
                "steps": args.e2e_steps, "api": "prand_generate_host_u32 / _f32 into page-locked host arrays",
-               "call_ms": {k: statistics.median(v) for k, v in call_ms.items()}}
+               "call_ms": {k: statistics.median(v) for k, v in call_ms.items()},
+               "call_ms_each": {k: [round(x, 2) for x in v] for k, v in call_ms.items()}}
         del hu, hf
 
     for h in handles.values():
