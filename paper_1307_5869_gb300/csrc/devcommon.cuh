@@ -199,61 +199,77 @@ __device__ __forceinline__ void store4<double>(double *p, double a, double b, do
 // ---------------------------------------------------------------- row staging
 // Thread-per-stream generators produce one row of outputs per lane; written
 // directly, a warp store would scatter 32 small pieces over 32 rows.  Instead
-// each lane stages 128 bytes of its row in a padded shared-memory tile (pitch
-// 144 B, so 16-byte accesses are bank-conflict free on both sides) and the warp
-// writes the tile out as whole 128-byte row segments, four rows per store.
-constexpr int kTilePitch = 144;
-constexpr int kTileBytes = 32 * kTilePitch;  // per warp
-
-template <typename OutT>
+// each lane stages ROWB bytes (128 or 256) of its row in a padded shared-memory
+// tile (pitch ROWB + 16, so 16-byte accesses are bank-conflict free on both
+// sides) and the warp writes the tile out as whole ROWB-byte row segments,
+// 512 / ROWB rows per store.  Longer segments suit HBM better; shorter ones
+// need half the shared memory.
+template <typename OutT, int ROWB = 128>
 struct RowFill {
-    static constexpr int K = 128 / (int)sizeof(OutT);  // outputs per row chunk
-    static constexpr int E = 16 / (int)sizeof(OutT);   // outputs per 16-byte vector
+    static constexpr int K = ROWB / (int)sizeof(OutT);  // outputs per row chunk
+    static constexpr int E = 16 / (int)sizeof(OutT);    // outputs per 16-byte vector
+    static constexpr int PITCH = ROWB + 16;             // tile bytes per row
+    static constexpr int TILE = 32 * PITCH;             // tile bytes per warp
+    static constexpr int PIECES = ROWB / 16;            // 16-byte pieces per row segment
+    static constexpr int ROWS = 32 / PIECES;            // row segments per warp store
 };
+constexpr int kTileBytes = RowFill<uint32_t, 128>::TILE;  // per warp, 128-byte segments
 
 // Emits `len` outputs of this lane's stream to dst (16-byte aligned rows), all
 // 32 lanes of the warp taking part (lanes with len 0 only help store).
-// next() returns the next 32-bit output; cvt converts it.
-template <typename OutT, typename Next, typename Conv>
+// next() returns the next 32-bit output; cvt converts it.  tile: the warp's
+// RowFill<OutT, ROWB>::TILE bytes of shared memory.
+template <typename OutT, int ROWB = 128, typename Next, typename Conv>
 __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, uint64_t len, unsigned char *tile, int lane)
 {
-    constexpr int K = RowFill<OutT>::K, E = RowFill<OutT>::E;
+    using RF = RowFill<OutT, ROWB>;
+    constexpr int K = RF::K, E = RF::E, PITCH = RF::PITCH, PIECES = RF::PIECES, ROWS = RF::ROWS;
     uint64_t maxlen = len;
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) maxlen = max(maxlen, (uint64_t)__shfl_xor_sync(kFull, (unsigned long long)maxlen, d));
     const uint64_t nch = (maxlen + K - 1) / K;
-    unsigned char *myrow = tile + lane * kTilePitch;
+    unsigned char *myrow = tile + lane * PITCH;
+    const int piece = lane % PIECES;
     for (uint64_t ch = 0; ch < nch; ++ch) {
         const uint32_t cnt = len > ch * K ? (uint32_t)min((uint64_t)K, len - ch * K) : 0u;
+        const unsigned long long mydst = (unsigned long long)(dst + ch * K);
         if (__all_sync(kFull, cnt == (uint32_t)K)) {
-            // every lane has a whole chunk: no per-output tests
+            // every lane has a whole chunk: no per-output tests, and every row
+            // segment of the tile is stored whole
 #pragma unroll
-            for (int v = 0; v < K / E; ++v) {
+            for (int v = 0; v < PIECES; ++v) {
                 OutT vals[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) vals[e] = cvt(next());
                 *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
             }
-        } else {
+            __syncwarp();
 #pragma unroll
-            for (int v = 0; v < K / E; ++v) {
-                if ((uint32_t)(v * E) < cnt) {
-                    OutT vals[E];
+            for (int i = 0; i < PIECES; ++i) {
+                const int r = ROWS * i + lane / PIECES;
+                OutT *rd = (OutT *)__shfl_sync(kFull, mydst, r);
+                *reinterpret_cast<uint4 *>(rd + piece * E) = *reinterpret_cast<const uint4 *>(tile + r * PITCH + 16 * piece);
+            }
+            __syncwarp();
+            continue;
+        }
 #pragma unroll
-                    for (int e = 0; e < E; ++e) vals[e] = (uint32_t)(v * E + e) < cnt ? cvt(next()) : OutT(0);
-                    *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
-                }
+        for (int v = 0; v < PIECES; ++v) {
+            if ((uint32_t)(v * E) < cnt) {
+                OutT vals[E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) vals[e] = (uint32_t)(v * E + e) < cnt ? cvt(next()) : OutT(0);
+                *reinterpret_cast<uint4 *>(myrow + 16 * v) = *reinterpret_cast<const uint4 *>(vals);
             }
         }
         __syncwarp();
-        const unsigned long long mydst = (unsigned long long)(dst + ch * K);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = 4 * i + (lane >> 3);
+        for (int i = 0; i < PIECES; ++i) {
+            const int r = ROWS * i + lane / PIECES;
             OutT *rd = (OutT *)__shfl_sync(kFull, mydst, r);
             const uint32_t rc = __shfl_sync(kFull, cnt, r);
-            const int col = (lane & 7) * E;
-            const unsigned char *src = tile + r * kTilePitch + 16 * (lane & 7);
+            const int col = piece * E;
+            const unsigned char *src = tile + r * PITCH + 16 * piece;
             if ((uint32_t)(col + E) <= rc) {
                 *reinterpret_cast<uint4 *>(rd + col) = *reinterpret_cast<const uint4 *>(src);
             } else {
@@ -266,9 +282,10 @@ __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, ui
     }
 }
 
-// Resident threads of a 256-thread kernel on the current device, computed once
-// per kernel and device (ID tells the kernels apart).
-template <int ID, typename K>
+// Resident threads of a kernel launched with BS-thread blocks on the current
+// device, computed once per kernel and device (ID tells the kernels apart: the
+// generator id for the per-handle fills, 100 and up for the others).
+template <int ID, int BS = 256, typename K>
 inline uint64_t resident_threads(K kernel)
 {
     constexpr int kDevs = 64;
@@ -281,8 +298,8 @@ inline uint64_t resident_threads(K kernel)
     }
     int sms = 152, bps = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, 0) != cudaSuccess || bps < 1) bps = 1;
-    const uint64_t c = (uint64_t)sms * bps * 256;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, BS, 0) != cudaSuccess || bps < 1) bps = 1;
+    const uint64_t c = (uint64_t)sms * bps * BS;
     if (dev >= 0 && dev < kDevs) cache[dev].store(c, std::memory_order_relaxed);
     return c;
 }

@@ -209,14 +209,19 @@ __global__ void lfsr_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t 
     for (int c = 0; c < 4; ++c) state[c * n + j] = z[c];
 }
 
+// LFSR113 fills are bound by HBM and the store path: 256-byte row segments,
+// 128-thread blocks (so the four warps' tiles stay within static shared memory).
+constexpr int kLfsrRowBytes = 256;
+constexpr unsigned kLfsrBlock = 128;
+
 template <typename OutT, bool ROWS = false>
-__global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
+__global__ void __launch_bounds__(kLfsrBlock) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
                                                        uint64_t stride, uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                        OutT *__restrict__ out, int vec)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ROWS) {
-        __shared__ __align__(16) unsigned char tiles[8][kTileBytes];
+        __shared__ __align__(16) unsigned char tiles[kLfsrBlock / 32][RowFill<OutT, kLfsrRowBytes>::TILE];
         const bool live = tid < nstreams * nsec;
         const uint64_t j = live ? tid % nstreams : 0;
         const uint64_t start = live ? (tid / nstreams) * seclen : 0;
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(256) lfsr_gen_kernel(const uint32_t *__restric
                 z0 = z[0]; z1 = z[1]; z2 = z[2]; z3 = z[3];
             }
         }
-        fill_rows<OutT>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
+        fill_rows<OutT, kLfsrRowBytes>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
                         out + j * nper + start, len, tiles[threadIdx.x >> 5], threadIdx.x & 31);
         if (len && start + len == nper) {
             sout[j] = z0; sout[stride + j] = z1; sout[2 * stride + j] = z2; sout[3 * stride + j] = z3;
@@ -333,7 +338,7 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
     if (R.nsec == 0) {
         // size by the rows form (the other form has the same footprint or less)
         const uint64_t cap = gen == PRAND_MRG32K3A ? resident_threads<1>(mrg_gen_kernel<OutT, true>)
-                                                   : resident_threads<2>(lfsr_gen_kernel<OutT, true>);
+                                                   : resident_threads<2, kLfsrBlock>(lfsr_gen_kernel<OutT, true>);
         pick_sections(R.count, nper, cap, &R.nsec, &R.seclen);
     }
     const uint32_t nsec = R.nsec;
@@ -349,8 +354,9 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
         if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
         else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     } else {
-        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
-        else lfsr_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        const unsigned BL = kLfsrBlock;
+        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, BL), BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        else lfsr_gen_kernel<OutT><<<grid_for(threads, BL), BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
     }
     return launch_check();
 }
@@ -442,7 +448,7 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     if (n_per_stream == 0) return PRAND_OK;
     uint32_t nsec;
     uint64_t seclen;
-    pick_sections(n_streams, n_per_stream, resident_threads<3>(mrg_gen_kernel<uint32_t>), &nsec, &seclen);
+    pick_sections(n_streams, n_per_stream, resident_threads<100>(mrg_gen_kernel<uint32_t>), &nsec, &seclen);
     int vec = ((uintptr_t)dev_out % 16) == 0;
     const unsigned B = 256;
     uint32_t *sout = nsec > 1 ? D->next : dev_state;

@@ -135,12 +135,22 @@ __device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint3
     for (int c = 0; c < 4; ++c) z[c] = gf2_apply(tab + ((size_t)c * kJumpBits + b) * 32, z[c]);
 }
 
+// The same word step with one funnel shift: the masked part, (z & mask) << S,
+// holds bits [32 - R, 32) and ((z << Q) ^ z) >> R bits [0, 32 - R) (R = P - S),
+// so the new word is the low half of the 64-bit value (z >> (32 - P) : b) >> R,
+// b = (z << Q) ^ z -- four operations instead of five.
+template <int P, int Q, int S>
+__device__ __forceinline__ uint32_t taus_step_funnel(uint32_t z)
+{
+    return __funnelshift_r((z << Q) ^ z, z >> (32 - P), P - S);
+}
+
 __device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)
 {
-    z0 = taus_step<31, 6, 18>(z0);
-    z1 = taus_step<29, 2, 2>(z1);
-    z2 = taus_step<28, 13, 7>(z2);
-    z3 = taus_step<25, 3, 13>(z3);
+    z0 = taus_step_funnel<31, 6, 18>(z0);
+    z1 = taus_step_funnel<29, 2, 2>(z1);
+    z2 = taus_step_funnel<28, 13, 7>(z2);
+    z3 = taus_step_funnel<25, 3, 13>(z3);
     return z0 ^ z1 ^ z2 ^ z3;
 }
 
