@@ -7,11 +7,64 @@
 // GF(2) powers of the LFSR word step), exactly as the paper's array fill
 // splits an array into sections (Sec. 6).  State is stored structure-of-arrays
 // (word c of stream j at state[c * nstreams + j]) so a warp loads it coalesced.
+#include <array>
 #include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "mrg_lfsr_dev.cuh"
 
 namespace prand {
+
+// ------------------------------------------------ section jumps of one fill
+// The sections of a fill start at s * seclen (s = 1 .. nsec - 1) in every
+// stream, so the jump to each section start is the same matrix for all
+// streams.  For up to kSecJumps sections these matrices are built once on the
+// host and passed as a kernel parameter: a section thread then applies one
+// matrix instead of one table entry per set bit of its offset.
+constexpr int kSecJumps = 15;
+struct NoSecJumps {
+    static constexpr int kCount = 0;
+};
+struct LfsrSecJumps {
+    static constexpr int kCount = kSecJumps;
+    uint32_t col[kSecJumps][4][32];  // [s - 1][component][bit]: image of bit i under T_c^(s seclen)
+};
+struct MrgSecJumps {
+    static constexpr int kCount = kSecJumps;
+    uint32_t m[kSecJumps][18];  // [s - 1]: A^(s seclen) mod m1, B^(s seclen) mod m2, row-major
+};
+
+template <typename SJ>
+__device__ __forceinline__ void lfsr_jump_section(const uint32_t *tab, const SJ &sj, uint64_t sec, uint64_t start,
+                                                  uint32_t z[4])
+{
+    if constexpr (SJ::kCount > 0) {
+        if (sec <= (uint64_t)SJ::kCount) {
+            for (int c = 0; c < 4; ++c) z[c] = gf2_apply(sj.col[sec - 1][c], z[c]);
+            return;
+        }
+    }
+    for (int b = 0; b < 64; ++b)
+        if ((start >> b) & 1u) lfsr_apply_bit(tab, b, z);
+}
+
+template <typename SJ>
+__device__ __forceinline__ void mrg_jump_section(const uint32_t *tab, const SJ &sj, uint64_t sec, uint64_t start,
+                                                 uint32_t x[3], uint32_t y[3])
+{
+    if constexpr (SJ::kCount > 0) {
+        if (sec <= (uint64_t)SJ::kCount) {
+            mat3_vec<209>(sj.m[sec - 1], x);
+            mat3_vec<22853>(sj.m[sec - 1] + 9, y);
+            return;
+        }
+    }
+    for (int b = 0; b < 64; ++b)
+        if ((start >> b) & 1u) mrg_apply_bit(tab, b, x, y);
+}
 
 // =========================================================== MRG32K3A
 // tab[b] = (A^(2^b) mod m1, B^(2^b) mod m2), b < kJumpBits.
@@ -83,10 +136,10 @@ __global__ void mrg_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t n
 // last one may be shorter); the thread of the last section writes the stream's
 // next state to sout, a separate buffer when a stream has several sections (so
 // no thread reads a state that another thread has already replaced).
-template <typename OutT, bool ROWS = false>
+template <typename OutT, bool ROWS = false, typename SJ = NoSecJumps>
 __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
                                                       uint64_t stride, uint64_t nper, uint32_t nsec, uint64_t seclen,
-                                                      OutT *__restrict__ out, int vec)
+                                                      OutT *__restrict__ out, int vec, const __grid_constant__ SJ sj)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ROWS) {
@@ -102,8 +155,7 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
             y0 = state[3 * stride + j]; y1 = state[4 * stride + j]; y2 = state[5 * stride + j];
             if (start) {
                 uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
-                for (int b = 0; b < 64; ++b)
-                    if ((start >> b) & 1u) mrg_apply_bit(tab, b, x, y);
+                mrg_jump_section(tab, sj, tid / nstreams, start, x, y);
                 x0 = x[0]; x1 = x[1]; x2 = x[2]; y0 = y[0]; y1 = y[1]; y2 = y[2];
             }
         }
@@ -126,8 +178,7 @@ __global__ void __launch_bounds__(256) mrg_gen_kernel(const uint32_t *__restrict
     uint32_t y0 = state[3 * stride + j], y1 = state[4 * stride + j], y2 = state[5 * stride + j];
     if (start) {
         uint32_t x[3] = { x0, x1, x2 }, y[3] = { y0, y1, y2 };
-        for (int b = 0; b < 64; ++b)
-            if ((start >> b) & 1u) mrg_apply_bit(tab, b, x, y);
+        mrg_jump_section(tab, sj, sec, start, x, y);
         x0 = x[0]; x1 = x[1]; x2 = x[2]; y0 = y[0]; y1 = y[1]; y2 = y[2];
     }
     OutT *o = out + j * nper + start;
@@ -214,10 +265,10 @@ __global__ void lfsr_skip_kernel(const uint32_t *tab, uint32_t *state, uint64_t 
 constexpr int kLfsrRowBytes = 256;
 constexpr unsigned kLfsrBlock = 128;
 
-template <typename OutT, bool ROWS = false>
+template <typename OutT, bool ROWS = false, typename SJ = NoSecJumps>
 __global__ void __launch_bounds__(kLfsrBlock) lfsr_gen_kernel(const uint32_t *__restrict__ tab, const uint32_t *state, uint32_t *sout, uint64_t nstreams,
                                                        uint64_t stride, uint64_t nper, uint32_t nsec, uint64_t seclen,
-                                                       OutT *__restrict__ out, int vec)
+                                                       OutT *__restrict__ out, int vec, const __grid_constant__ SJ sj)
 {
     uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ROWS) {
@@ -231,8 +282,7 @@ __global__ void __launch_bounds__(kLfsrBlock) lfsr_gen_kernel(const uint32_t *__
             z0 = state[j]; z1 = state[stride + j]; z2 = state[2 * stride + j]; z3 = state[3 * stride + j];
             if (start) {
                 uint32_t z[4] = { z0, z1, z2, z3 };
-                for (int b = 0; b < 64; ++b)
-                    if ((start >> b) & 1u) lfsr_apply_bit(tab, b, z);
+                lfsr_jump_section(tab, sj, tid / nstreams, start, z);
                 z0 = z[0]; z1 = z[1]; z2 = z[2]; z3 = z[3];
             }
         }
@@ -252,8 +302,7 @@ __global__ void __launch_bounds__(kLfsrBlock) lfsr_gen_kernel(const uint32_t *__
     uint32_t z0 = state[j], z1 = state[stride + j], z2 = state[2 * stride + j], z3 = state[3 * stride + j];
     if (start) {
         uint32_t z[4] = { z0, z1, z2, z3 };
-        for (int b = 0; b < 64; ++b)
-            if ((start >> b) & 1u) lfsr_apply_bit(tab, b, z);
+        lfsr_jump_section(tab, sj, sec, start, z);
         z0 = z[0]; z1 = z[1]; z2 = z[2]; z3 = z[3];
     }
     OutT *o = out + j * nper + start;
@@ -315,6 +364,119 @@ prand_status_t mrg_lfsr_skip(int gen, const DevTables *T, void *d_state, uint64_
     return launch_check();
 }
 
+// Host construction of the section jumps, cached per (generator, seclen,
+// nsec): M^(s seclen) for s = 1 .. nsec - 1 by square-and-multiply.
+namespace {
+
+using Gf2Mat = std::array<uint32_t, 32>;  // columns: image of bit i
+
+Gf2Mat gf2_mul(const Gf2Mat &X, const Gf2Mat &Y)  // X Y: Y first, then X
+{
+    Gf2Mat R;
+    for (int i = 0; i < 32; ++i) {
+        uint32_t v = Y[i], r = 0;
+        for (int b = 0; b < 32; ++b)
+            if ((v >> b) & 1u) r ^= X[b];
+        R[i] = r;
+    }
+    return R;
+}
+
+uint32_t lfsr_comp_step_host(int c, uint32_t z)
+{
+    switch (c) {
+    case 0: return taus_step<31, 6, 18>(z);
+    case 1: return taus_step<29, 2, 2>(z);
+    case 2: return taus_step<28, 13, 7>(z);
+    default: return taus_step<25, 3, 13>(z);
+    }
+}
+
+using Mat3 = std::array<uint64_t, 9>;
+
+Mat3 mat3_mul(const Mat3 &X, const Mat3 &Y, uint64_t m)
+{
+    Mat3 R;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            uint64_t s = 0;
+            for (int k = 0; k < 3; ++k) s = (s + X[3 * i + k] * Y[3 * k + j] % m) % m;
+            R[3 * i + j] = s;
+        }
+    return R;
+}
+
+template <typename M, typename Mul>
+M mat_pow(M base, uint64_t e, M one, Mul mul)
+{
+    M r = one;
+    while (e) {
+        if (e & 1u) r = mul(r, base);
+        base = mul(base, base);
+        e >>= 1;
+    }
+    return r;
+}
+
+std::mutex g_sj_mu;
+std::map<std::tuple<int, uint64_t, uint32_t>, LfsrSecJumps> g_sj_lfsr;
+std::map<std::tuple<int, uint64_t, uint32_t>, MrgSecJumps> g_sj_mrg;
+constexpr size_t kSecJumpCacheMax = 256;
+
+void build_sec_jumps(uint64_t seclen, uint32_t nsec, LfsrSecJumps *out)
+{
+    Gf2Mat id;
+    for (int i = 0; i < 32; ++i) id[i] = 1u << i;
+    for (int c = 0; c < 4; ++c) {
+        Gf2Mat M;
+        for (int i = 0; i < 32; ++i) M[i] = lfsr_comp_step_host(c, 1u << i);
+        const Gf2Mat A = mat_pow(M, seclen, id, gf2_mul);
+        Gf2Mat J = A;
+        for (uint32_t s = 1; s < nsec && s <= (uint32_t)kSecJumps; ++s) {
+            for (int i = 0; i < 32; ++i) out->col[s - 1][c][i] = J[i];
+            J = gf2_mul(J, A);
+        }
+    }
+}
+
+void build_sec_jumps(uint64_t seclen, uint32_t nsec, MrgSecJumps *out)
+{
+    const Mat3 one = { 1, 0, 0, 0, 1, 0, 0, 0, 1 };
+    const Mat3 a = { 0, 1403580, kM1 - 810728, 1, 0, 0, 0, 1, 0 };
+    const Mat3 b = { 527612, 0, kM2 - 1370589, 1, 0, 0, 0, 1, 0 };
+    auto mul1 = [](const Mat3 &X, const Mat3 &Y) { return mat3_mul(X, Y, kM1); };
+    auto mul2 = [](const Mat3 &X, const Mat3 &Y) { return mat3_mul(X, Y, kM2); };
+    const Mat3 A = mat_pow(a, seclen, one, mul1), B = mat_pow(b, seclen, one, mul2);
+    Mat3 JA = A, JB = B;
+    for (uint32_t s = 1; s < nsec && s <= (uint32_t)kSecJumps; ++s) {
+        for (int i = 0; i < 9; ++i) {
+            out->m[s - 1][i] = (uint32_t)JA[i];
+            out->m[s - 1][9 + i] = (uint32_t)JB[i];
+        }
+        JA = mul1(JA, A);
+        JB = mul2(JB, B);
+    }
+}
+
+template <typename SJ>
+void sec_jumps(std::map<std::tuple<int, uint64_t, uint32_t>, SJ> &cache, int gen, uint64_t seclen, uint32_t nsec,
+               SJ *out)
+{
+    const auto key = std::make_tuple(gen, seclen, nsec);
+    std::lock_guard<std::mutex> g(g_sj_mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        if (cache.size() >= kSecJumpCacheMax) cache.clear();
+        SJ sj;
+        std::memset(&sj, 0, sizeof sj);
+        build_sec_jumps(seclen, nsec, &sj);
+        it = cache.emplace(key, sj).first;
+    }
+    *out = it->second;
+}
+
+}  // namespace
+
 // Sections per stream: whole waves of the kernel's resident threads (cap),
 // sections no shorter than 256 outputs and starting on multiples of 32
 // outputs, so the staged 128-byte row stores of every section fill whole
@@ -350,13 +512,30 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
     // staged row stores need every row start 16-byte aligned
     constexpr uint64_t E = RowFill<OutT>::E;
     const bool rows = ((uintptr_t)out % 16) == 0 && nper % E == 0 && seclen % E == 0;
+    // section jumps as one matrix per section when there are few sections
+    const bool sj = nsec > 1 && nsec <= (uint32_t)kSecJumps + 1;
     if (gen == PRAND_MRG32K3A) {
-        if (rows) mrg_gen_kernel<OutT, true><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
-        else mrg_gen_kernel<OutT><<<grid_for(threads, B), B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        const unsigned g = grid_for(threads, B);
+        if (sj) {
+            MrgSecJumps J;
+            sec_jumps(g_sj_mrg, gen, seclen, nsec, &J);
+            if (rows) mrg_gen_kernel<OutT, true, MrgSecJumps><<<g, B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, J);
+            else mrg_gen_kernel<OutT, false, MrgSecJumps><<<g, B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, J);
+        } else {
+            if (rows) mrg_gen_kernel<OutT, true><<<g, B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, NoSecJumps{});
+            else mrg_gen_kernel<OutT><<<g, B, 0, st>>>(T->mrg, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, NoSecJumps{});
+        }
     } else {
-        const unsigned BL = kLfsrBlock;
-        if (rows) lfsr_gen_kernel<OutT, true><<<grid_for(threads, BL), BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
-        else lfsr_gen_kernel<OutT><<<grid_for(threads, BL), BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec);
+        const unsigned BL = kLfsrBlock, g = grid_for(threads, BL);
+        if (sj) {
+            LfsrSecJumps J;
+            sec_jumps(g_sj_lfsr, gen, seclen, nsec, &J);
+            if (rows) lfsr_gen_kernel<OutT, true, LfsrSecJumps><<<g, BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, J);
+            else lfsr_gen_kernel<OutT, false, LfsrSecJumps><<<g, BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, J);
+        } else {
+            if (rows) lfsr_gen_kernel<OutT, true><<<g, BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, NoSecJumps{});
+            else lfsr_gen_kernel<OutT><<<g, BL, 0, st>>>(T->lfsr, sin, sout, nstreams, R.stride, nper, nsec, seclen, out, vec, NoSecJumps{});
+        }
     }
     return launch_check();
 }
@@ -453,7 +632,8 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     const unsigned B = 256;
     uint32_t *sout = nsec > 1 ? D->next : dev_state;
     mrg_gen_kernel<uint32_t><<<grid_for(n_streams * nsec, B), B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_streams,
-                                                                          n_per_stream, nsec, seclen, dev_out, vec);
+                                                                          n_per_stream, nsec, seclen, dev_out, vec,
+                                                                          NoSecJumps{});
     if ((s = launch_check()) != PRAND_OK) return s;
     if (nsec > 1) {
         mrg_copy_words_kernel<<<grid_for(6 * n_streams, B), B, 0, st>>>(D->next, dev_state, 6 * n_streams);
