@@ -37,7 +37,7 @@ WORKLOAD = ("bulk fill: MT19937, LFSR113, GM61; 2^20 block-split streams x (2^10
             "outputs per generator per GPU per step; seed 0x9E3779B97F4A7C15; rank r takes streams "
             "[r 2^20, (r+1) 2^20)")
 
-# Algorithmic work per output (measurement section).
+# Algorithmic work per output: bytes of generator state per stream (loaded and stored once per fill).
 STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 16, "GM29": 32 * 16,
                "GM31": 32 * 16, "GM55": 8 * 16, "GM61": 32 * 16, "GQ58_1": 32 * 16, "GQ58_3": 12 * 16,
                "GQ58_4": 8 * 16}
@@ -49,11 +49,11 @@ STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 1
 GM61_OPS_PER_WORD = 16 * 32
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) per stream of one fill of 1024 outputs, from one ncu
-# capture of the current kernels at that shape (profiles/traffic_bulk_fill.md);
-# None for other shapes.
-TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.3205e9 / 2**18, "MT19937.f32": 2.3185e9 / 2**18,
-                           "LFSR113.u32": 1.0263e9 / 2**18, "LFSR113.f32": 1.0264e9 / 2**18,
-                           "GM61.u32": 1.2774e9 / 2**18, "GM61.f32": 1.2790e9 / 2**18}
+# capture of the current kernels at the benchmark's shape, 2^20 streams
+# (profiles/traffic_bulk_fill.md); None for other shapes.
+TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 9.466e9 / 2**20, "MT19937.f32": 9.467e9 / 2**20,
+                           "LFSR113.u32": 4.264e9 / 2**20, "LFSR113.f32": 4.264e9 / 2**20,
+                           "GM61.u32": 5.310e9 / 2**20, "GM61.f32": 5.311e9 / 2**20}
 # Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
