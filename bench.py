@@ -288,6 +288,22 @@ def run_gpu(args):
     samples_step = len(gens) * 2 * nS * nP
     value = world * samples_step * args.steps / (total_ms * 1e-3) / 1e9
 
+    # ----- context: a plain write-only fill of the same u32 buffer (torch's fill_),
+    # the rate a kernel that only writes can reach on this GPU; reported beside
+    # the rooflines, whose peak stays the measured copy bandwidth
+    for _ in range(3):
+        U.fill_(0)
+    fill_ms = []
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        U.fill_(0)
+        b.record(stream)
+        b.synchronize()
+        fill_ms.append(a.elapsed_time(b))
+    write_fill_bytes = U.numel() * 4
+    write_fill_gbs = write_fill_bytes / (statistics.median(fill_ms) * 1e-3) / 1e9
+
     # ----- rooflines (per launch, live CUDA-event durations)
     hbm_peak, peak_src = _peaks()
     rooflines = {}
@@ -295,8 +311,10 @@ def run_gpu(args):
         for dt, ms in (("u32", ms_u[g]), ("f32", ms_f[g])):
             key = f"{g}.{dt}"
             if g.startswith("GM") or g.startswith("GQ"):
-                ops = nS * nP * GM61_OPS_PER_WORD
-                rooflines[key] = {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12,
+                # the int32 operation count is derived for GM61 only; the other
+                # ensembles (custom runs) report their rate without a fraction
+                ops = nS * nP * GM61_OPS_PER_WORD if g == "GM61" else None
+                rooflines[key] = {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12 if ops else None,
                                   "peak": SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
                                   "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9}
             else:
@@ -304,9 +322,12 @@ def run_gpu(args):
                 rooflines[key] = {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm_peak,
                                   "unit": "GB/s", "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9,
                                   "traffic": None}
-            rooflines[key]["frac"] = rooflines[key]["achieved"] / rooflines[key]["peak"]
+            ach = rooflines[key]["achieved"]
+            rooflines[key]["frac"] = ach / rooflines[key]["peak"] if ach is not None else None
             tr = TRAFFIC_PER_STREAM_1024.get(key) if nP == 1024 else None
             rooflines[key]["traffic"] = tr * nS if tr else None
+            if rooflines[key]["bound"] == "hbm":
+                rooflines[key]["frac_of_write_fill"] = rooflines[key]["achieved"] / write_fill_gbs
     # dominant kernel = the launch with the largest share of the step
     dom = max(rooflines, key=lambda k: rooflines[k]["ms"])
     R = rooflines[dom]
@@ -384,6 +405,8 @@ def run_gpu(args):
                        "parallelism": f"{world} GPU(s), disjoint stream ranges, no collective"},
             "roofline": roofline,
             "rooflines": rooflines,
+            "write_fill": {"gb_per_s": write_fill_gbs, "bytes": write_fill_bytes,
+                           "what": "torch fill_ of the u32 output buffer, write only, median of 10 (context)"},
             "per_generator_gsamples_per_s": per_gen,
             "init_ms": init_ms,
             "gpu_launches": launches,

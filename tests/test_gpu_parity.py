@@ -152,6 +152,18 @@ def test_error_paths_on_device():
 
 
 @pytest.mark.parametrize("gen", GENS)
+def test_extreme_stream_indices(gen):
+    # the largest stream indices the ABI accepts (beyond Table 4, so the call
+    # warns): the jump offset (first + j) L needs up to 64 + log2(L) bits,
+    # 2^496 for MT19937
+    for seed, first, n, dt in ((12345, 2**64 - 3, 2, "u32"), (7, 10**19 - 1, 1, "f64")):
+        g = P.Generator(gen, seed, first, n)
+        _assert_same(_gpu(g.generate(64, dt)), O.Streams(gen, seed, first, n).generate(dt, 64), dt,
+                     f"{gen} streams {first}..{first + n - 1}")
+        g.close()
+
+
+@pytest.mark.parametrize("gen", GENS)
 def test_table4_streams_2_pow_16_by_2_pow_12_sampled(gen):
     # all eleven generators, 2^16 block-split streams x 2^12 outputs (u32 and f32),
     # seed 12345; sampled streams against the oracle's stream k = base + k * L
