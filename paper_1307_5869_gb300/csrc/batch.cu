@@ -307,7 +307,7 @@ prand_status_t engine_get(Engine **out)
         E.device = dev;
         prand_status_t s = get_tables(PRAND_MT19937, &E.T);
         if (s != PRAND_OK) return s;
-        if (cudaMalloc(&E.d_counter, 64) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (!dev_alloc(&E.d_counter, 64)) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
         cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev);
         for (int m = 0; m < 2; ++m) {
@@ -352,7 +352,7 @@ prand_status_t engine_bases(Engine &E, uint64_t seed, cudaStream_t st, const See
         B.off[g] = total;
         total += (state_bytes_per_stream(g) + 255) & ~(size_t)255;
     }
-    if (cudaMalloc(&B.dev, total) != cudaSuccess) return PRAND_ERR_NOMEM;
+    if (!dev_alloc(&B.dev, total)) return PRAND_ERR_NOMEM;
     prand_status_t s = PRAND_OK;
     for (int g = 0; g < PRAND_NUM_GENERATORS && s == PRAND_OK; ++g) {
         void *p = (char *)B.dev + B.off[g];
@@ -544,13 +544,13 @@ prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st
     if (n > E->h_cap) {
         if (E->h_tiles) cudaFreeHost(E->h_tiles);
         E->h_cap = std::max<size_t>(n, 2 * E->h_cap);
-        if (cudaMallocHost(&E->h_tiles, E->h_cap * sizeof(BatchTile)) != cudaSuccess) { E->h_cap = 0; E->h_tiles = nullptr; return PRAND_ERR_NOMEM; }
+        if (!host_alloc(&E->h_tiles, E->h_cap * sizeof(BatchTile))) { E->h_cap = 0; E->h_tiles = nullptr; return PRAND_ERR_NOMEM; }
     }
     if (n > E->d_cap) {
         // the previous batch may still read the old buffer: free it in stream order
         if (E->d_tiles) { cudaStreamSynchronize(st); cudaFree(E->d_tiles); }
         E->d_cap = std::max<size_t>(n, 2 * E->d_cap);
-        if (cudaMalloc(&E->d_tiles, E->d_cap * sizeof(BatchTile)) != cudaSuccess) { E->d_cap = 0; E->d_tiles = nullptr; return PRAND_ERR_NOMEM; }
+        if (!dev_alloc(&E->d_tiles, E->d_cap * sizeof(BatchTile))) { E->d_cap = 0; E->d_tiles = nullptr; return PRAND_ERR_NOMEM; }
     }
     if (n) {
         memcpy(E->h_tiles, tiles.data(), n * sizeof(BatchTile));
@@ -635,13 +635,13 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     if (tiles.size() > 0xFFFFFFFFull) return fail(PRAND_ERR_ARG);
     p->ntiles = (uint32_t)tiles.size();
     p->nmt = count_mt_tiles(tiles);
-    if (cudaMalloc(&p->d_counter, 64) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+    if (!dev_alloc(&p->d_counter, 64)) return fail(PRAND_ERR_NOMEM);
     if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
         return fail(PRAND_ERR_CUDA);
     if (p->ntiles) {
-        if (cudaMalloc(&p->d_tiles, tiles.size() * sizeof(BatchTile)) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+        if (!dev_alloc(&p->d_tiles, tiles.size() * sizeof(BatchTile))) return fail(PRAND_ERR_NOMEM);
         if (cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(PRAND_ERR_CUDA);
     }
@@ -751,7 +751,7 @@ prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n
     size_t maxb = 0;
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) maxb = std::max(maxb, state_bytes_per_stream(g));
     void *scratch = nullptr;
-    if (n && cudaMalloc(&scratch, 2 * maxb * n) != cudaSuccess) return PRAND_ERR_NOMEM;
+    if (n && !dev_alloc(&scratch, 2 * maxb * n)) return PRAND_ERR_NOMEM;
     for (size_t i = 0; i < n && s == PRAND_OK; ++i) {
         const prand_request_t &r = reqs[i];
         if (!r.length) continue;

@@ -120,7 +120,7 @@ prand_status_t get_mt_window(DevTables *T)
     const uint32_t *host = mt_host_window_polys();
     if (!host) return PRAND_ERR_STATE;
     const size_t bytes = (size_t)kMtWinPositions * 16 * kMtPolyWords * sizeof(uint32_t);
-    if (cudaMalloc(&T->mt_win, bytes) != cudaSuccess) return PRAND_ERR_NOMEM;
+    if (!dev_alloc(&T->mt_win, bytes)) return PRAND_ERR_NOMEM;
     if (cudaMemcpy(T->mt_win, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
     T->ready_mt_win = true;
     return PRAND_OK;
@@ -137,10 +137,10 @@ prand_status_t get_tables(int gen, DevTables **out)
         size_t mrg_b = (size_t)kJumpBits * 18 * sizeof(uint32_t);
         size_t lfsr_b = (size_t)4 * kJumpBits * 32 * sizeof(uint32_t);
         size_t gm_b = (size_t)kJumpBits * 4 * sizeof(uint64_t);
-        if (cudaMalloc(&T.mrg, mrg_b) != cudaSuccess) return PRAND_ERR_NOMEM;
-        if (cudaMalloc(&T.lfsr, lfsr_b) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (!dev_alloc(&T.mrg, mrg_b)) return PRAND_ERR_NOMEM;
+        if (!dev_alloc(&T.lfsr, lfsr_b)) return PRAND_ERR_NOMEM;
         for (int g = 0; g < 8; ++g)
-            if (cudaMalloc(&T.gm[g], gm_b) != cudaSuccess) return PRAND_ERR_NOMEM;
+            if (!dev_alloc(&T.gm[g], gm_b)) return PRAND_ERR_NOMEM;
         prand_status_t s = mrg_build_table(T.mrg, 0);
         if (s == PRAND_OK) s = lfsr_build_table(T.lfsr, 0);
         for (int g = 0; g < 8 && s == PRAND_OK; ++g) s = gm_build_table(PRAND_GM19 + g, T.gm[g], 0);
@@ -152,7 +152,7 @@ prand_status_t get_tables(int gen, DevTables **out)
         const uint32_t *host = mt_host_pow2_polys();
         if (!host) return PRAND_ERR_STATE;
         size_t bytes = (size_t)kMtPolyCount * kMtPolyWords * sizeof(uint32_t);
-        if (cudaMalloc(&T.mt, bytes) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (!dev_alloc(&T.mt, bytes)) return PRAND_ERR_NOMEM;
         if (cudaMemcpy(T.mt, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
         T.ready_mt = true;
     }
@@ -277,7 +277,7 @@ prand_status_t ensure_staging(prand_handle_t h)
     h->stage_bytes = bytes;
     bool ok = cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking) == cudaSuccess;
     for (int b = 0; b < 2 && ok; ++b)
-        ok = cudaMalloc(&h->stage[b], bytes) == cudaSuccess &&
+        ok = dev_alloc(&h->stage[b], bytes) &&
              cudaEventCreateWithFlags(&h->ev_gen[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&h->ev_copy[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -380,7 +380,7 @@ prand_status_t prand_create(prand_handle_t *out, prand_gen_t gen, uint64_t seed)
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return PRAND_ERR_CUDA; }
     prand_status_t s = get_tables(h->gen, &h->T);
     if (s != PRAND_OK) { delete h; return s; }
-    if (cudaMalloc(&h->d_base, state_bytes_per_stream(h->gen)) != cudaSuccess) { delete h; return PRAND_ERR_NOMEM; }
+    if (!dev_alloc(&h->d_base, state_bytes_per_stream(h->gen))) { delete h; return PRAND_ERR_NOMEM; }
     Variant V;
     variant_params(h->gen, 0, &V);
     if (h->gen == PRAND_MT19937) s = mt_seed(seed, h->d_base, 0);
@@ -413,8 +413,8 @@ static prand_status_t init_layout(prand_handle_t h, int32_t layout, uint64_t fir
     free_states(h);
     uint64_t bytes;
     if (mul_overflows(n_streams, state_bytes_per_stream(h->gen), &bytes)) return PRAND_ERR_ARG;
-    if (cudaMalloc(&h->d_state, bytes) != cudaSuccess) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
-    if (h->gen != PRAND_MT19937 && cudaMalloc(&h->d_spare, bytes) != cudaSuccess) {
+    if (!dev_alloc(&h->d_state, bytes)) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
+    if (h->gen != PRAND_MT19937 && !dev_alloc(&h->d_spare, bytes)) {
         h->d_spare = nullptr;
         free_states(h);
         return PRAND_ERR_NOMEM;
@@ -586,8 +586,8 @@ prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t by
     if ((s = sync_last(h)) != PRAND_OK) return s;
     if (h->n != hd.n) {
         free_states(h);
-        if (cudaMalloc(&h->d_state, sb) != cudaSuccess) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
-        if (h->gen != PRAND_MT19937 && cudaMalloc(&h->d_spare, sb) != cudaSuccess) {
+        if (!dev_alloc(&h->d_state, sb)) { h->d_state = nullptr; return PRAND_ERR_NOMEM; }
+        if (h->gen != PRAND_MT19937 && !dev_alloc(&h->d_spare, sb)) {
             h->d_spare = nullptr;
             free_states(h);
             return PRAND_ERR_NOMEM;

@@ -12,6 +12,31 @@
 namespace prand {
 
 // ---------------------------------------------------------------------------
+// Allocation.  A refused cudaMalloc / cudaHostAlloc also leaves its error in
+// the runtime's per-thread last-error slot, where the next launch check
+// (cudaGetLastError) would find it and report a launch that succeeded as a
+// CUDA failure.  These wrappers clear it, so a refused allocation is reported
+// once, as PRAND_ERR_NOMEM by the caller, and later calls are unaffected.
+// ---------------------------------------------------------------------------
+template <typename T>
+inline bool dev_alloc(T **p, size_t bytes)
+{
+    if (cudaMalloc((void **)p, bytes) == cudaSuccess) return true;
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return false;
+}
+
+template <typename T>
+inline bool host_alloc(T **p, size_t bytes, unsigned flags = cudaHostAllocDefault)
+{
+    if (cudaHostAlloc((void **)p, bytes, flags) == cudaSuccess) return true;
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // Generator constants, restated from the paper.
 // ---------------------------------------------------------------------------
 

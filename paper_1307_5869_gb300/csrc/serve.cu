@@ -469,12 +469,12 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
     if (s != PRAND_OK) return fail(s);
     S->P = batch_params();
     S->out_cap = output_bytes & ~255ull;
-    if (cudaMalloc(&S->out_base, S->out_cap) != cudaSuccess) { S->out_base = nullptr; return fail(PRAND_ERR_NOMEM); }
+    if (!dev_alloc(&S->out_base, S->out_cap)) { S->out_base = nullptr; return fail(PRAND_ERR_NOMEM); }
     S->arena = Arena(S->out_cap);
     S->slot_cap = slots_per_generator;
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) {
         const size_t bytes = 2ull * slots_per_generator * slot_words(g) * 4;
-        if (cudaMalloc(&S->slot_arena[g], bytes) != cudaSuccess) { S->slot_arena[g] = nullptr; return fail(PRAND_ERR_NOMEM); }
+        if (!dev_alloc(&S->slot_arena[g], bytes)) { S->slot_arena[g] = nullptr; return fail(PRAND_ERR_NOMEM); }
         S->ctx.slots[g] = S->slot_arena[g];
         S->free_slots[g].reserve(slots_per_generator);
         for (uint32_t i = slots_per_generator; i-- > 0;) S->free_slots[g].push_back(i);
@@ -482,13 +482,13 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
     for (Flight &F : S->fl) {
         if (cudaStreamCreateWithFlags(&F.st, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
         if (cudaEventCreate(&F.ev) != cudaSuccess || cudaEventCreate(&F.ev0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-        if (cudaMalloc(&F.counter, 64) != cudaSuccess) return fail(PRAND_ERR_NOMEM);
+        if (!dev_alloc(&F.counter, 64)) return fail(PRAND_ERR_NOMEM);
         void *hd = nullptr;
-        if (cudaMallocHost(&F.h_tiles, kFlightTiles * sizeof(BatchTile)) != cudaSuccess ||
-            cudaMalloc(&F.d_tiles, kFlightTiles * sizeof(BatchTile)) != cudaSuccess ||
-            cudaMallocHost(&F.h_left, kFlightReqs * 4) != cudaSuccess ||
-            cudaMalloc(&F.d_left, kFlightReqs * 4) != cudaSuccess ||
-            cudaHostAlloc(&hd, kFlightReqs * 4, cudaHostAllocMapped) != cudaSuccess)
+        if (!host_alloc(&F.h_tiles, kFlightTiles * sizeof(BatchTile)) ||
+            !dev_alloc(&F.d_tiles, kFlightTiles * sizeof(BatchTile)) ||
+            !host_alloc(&F.h_left, kFlightReqs * 4) ||
+            !dev_alloc(&F.d_left, kFlightReqs * 4) ||
+            !host_alloc(&hd, kFlightReqs * 4, cudaHostAllocMapped))
             return fail(PRAND_ERR_NOMEM);
         F.h_done = (volatile uint32_t *)hd;
     }

@@ -99,7 +99,7 @@ prand_status_t import_states_dev(int gen, const void *in, uint64_t n, void *d_st
     prand_status_t s;
     if (gen == PRAND_MT19937) {
         uint32_t *bad = nullptr, h_bad = 0, idx = 0;
-        if (cudaMalloc(&bad, sizeof(uint32_t)) != cudaSuccess) return PRAND_ERR_NOMEM;
+        if (!dev_alloc(&bad, sizeof(uint32_t))) return PRAND_ERR_NOMEM;
         cudaMemsetAsync(bad, 0, sizeof(uint32_t), st);
         check_mt_idx<<<grid(n), kB, 0, st>>>((const uint32_t *)in, n, bad);
         s = launch_check();

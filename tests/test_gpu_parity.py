@@ -151,6 +151,49 @@ def test_error_paths_on_device():
     assert L.prand_destroy(h) == 0
 
 
+@pytest.mark.parametrize("gen", ["MT19937", "MRG32K3A", "LFSR113", "GM61"])
+def test_refused_allocation_reports_nomem_and_leaves_no_error(gen):
+    # 2^38 streams need terabytes of state: the allocation is refused and
+    # reported as PRAND_ERR_NOMEM, the handle holds no streams, and the calls
+    # after it succeed (the refused allocation leaves no CUDA error behind for
+    # a later launch check to report)
+    import ctypes
+    import torch
+    L = P.load()
+    h = ctypes.c_void_p()
+    assert L.prand_create(ctypes.byref(h), P.GENERATORS.index(gen), 9) == 0
+    buf = torch.zeros(4 * 300, dtype=torch.int32, device="cuda")
+    assert L.prand_init_streams(h, 0, 1 << 38) == 3
+    assert L.prand_generate_u32(h, buf.data_ptr(), 300, None) == 5
+    assert L.prand_init_streams(h, 2, 4) == 0
+    assert L.prand_generate_u32(h, buf.data_ptr(), 300, None) == 0
+    torch.cuda.synchronize()
+    _assert_same(_gpu(buf).reshape(4, 300), O.Streams(gen, 9, 2, 4).generate("u32", 300), "u32", f"{gen} after NOMEM")
+    assert L.prand_destroy(h) == 0
+
+
+def test_refused_server_arena_reports_nomem():
+    import ctypes
+    L = P.load()
+    srv = ctypes.c_void_p()
+    assert L.prand_server_create(ctypes.byref(srv), ctypes.c_uint64(3), ctypes.c_uint64(1 << 52), 4) == 3
+    assert not srv.value
+    # a server of ordinary size still works afterwards
+    s = P.prand_server_create(3, 64 << 20, 4)
+    try:
+        rid = P.prand_server_submit(s, "LFSR113", 11, 500, 0)
+        import time
+        t0 = time.time()
+        while not P.prand_server_query(s, rid)[0]:
+            assert time.time() - t0 < 60, "request did not complete"
+            time.sleep(0.001)
+        out = np.empty(500, dtype=np.int32)
+        P.prand_server_read(s, rid, out)
+    finally:
+        P.prand_server_destroy(s)
+    _assert_same(out, O.State.stream("LFSR113", 3, 11).u32(500), "u32", "server after NOMEM")
+
+
 @pytest.mark.parametrize("gen", GENS)
 def test_extreme_stream_indices(gen):
     # the largest stream indices the ABI accepts (beyond Table 4, so the call
