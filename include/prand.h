@@ -211,13 +211,16 @@ prand_status_t prand_set_state(prand_handle_t h, const void *host_buf, size_t by
  * Errors: PRAND_ERR_ARG. */
 prand_status_t prand_query(prand_handle_t h, uint64_t *first_stream, uint64_t *n_streams, uint64_t *position);
 
-/* Free the handle's device memory.  h == NULL is a no-op. */
+/* Free the handle's device memory (the handle's counterpart of the paper's
+ * state struct, Sec. 7.1, going out of scope).  h == NULL is a no-op; returns
+ * PRAND_OK. */
 prand_status_t prand_destroy(prand_handle_t h);
 
 /* A static English string for a status code. */
 const char *prand_status_string(prand_status_t status);
 
-/* Number of device kernels this library has launched in the process. */
+/* Number of device kernels this library has launched in the process (no
+ * counterpart in the paper; a launch count for benchmarks).  Cannot fail. */
 uint64_t prand_kernel_launches(void);
 
 /* The float maps on their own (Sec. 7.3 asks only for outputs uniform in
@@ -236,7 +239,10 @@ uint64_t prand_kernel_launches(void);
 #define PRAND_MAP_MRG_F64 3
 prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out, cudaStream_t stream);
 
-/* One batched request: `length` outputs of stream `stream` of generator `gen`
+/* ---- Batched requests (no counterpart in the paper: many streams of mixed
+ * generators in one launch; each request is the paper's block-split stream,
+ * Sec. 5 / Table 4, filled as in Sec. 6) ----
+ * One batched request: `length` outputs of stream `stream` of generator `gen`
  * (seeded with the batch's seed), starting at the stream's beginning, written
  * to dev_out (caller-owned, aligned to the element size of `dtype`). */
 typedef struct {
@@ -260,7 +266,8 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
 
 /* The same requests, one ordinary stream-initialisation launch and one
  * generation launch per request (no fusion, no persistent scheduling); the
- * comparison point for prand_batch_run.  Returns after the work completes. */
+ * comparison point for prand_batch_run.  Returns after the work completes.
+ * Errors: as prand_batch_run. */
 prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n, uint64_t seed,
                                            prand_stream_t stream);
 
@@ -274,15 +281,18 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *plan, const prand_req
 prand_status_t prand_batch_plan_launch(prand_batch_plan_t plan, prand_stream_t stream);
 prand_status_t prand_batch_plan_destroy(prand_batch_plan_t plan);
 
-/* Tile tuner: times the batch for each candidate section length (outputs per
- * lane for MRG32K3A/LFSR113, per lane group for GM/GQ), keeps the fastest for
- * later batches on this device, and reports it (any output pointer may be
- * NULL).  If the environment variable PRAND_TUNE_CACHE names a file, the
- * result is written there and read back by later processes. */
+/* Tile tuner (no counterpart in the paper): times the batch for each
+ * candidate section length (outputs per lane for MRG32K3A/LFSR113, per lane
+ * group for GM/GQ), keeps the fastest for later batches on this device, and
+ * reports it (any output pointer may be NULL).  If the environment variable
+ * PRAND_TUNE_CACHE names a file, the result is written there and read back by
+ * later processes.  The requests' outputs are written (several times).
+ * Errors: as prand_batch_run. */
 prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream,
                                     uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, float *best_ms);
 
-/* ---- Request server (continuous batching, resident streams) ----
+/* ---- Request server (no counterpart in the paper: continuous batching of
+ * stream requests, with stream states resident on the device) ----
  * A request (generator, stream index, length, element type) returns the next
  * `length` outputs of that stream: the server keeps each stream it has served
  * resident on the device and continues it on the next request; a stream seen
@@ -322,20 +332,28 @@ prand_status_t prand_server_create(prand_server_t *srv, uint64_t seed, uint64_t 
 prand_status_t prand_server_submit(prand_server_t srv, int32_t gen, uint64_t stream, uint64_t length, int32_t dtype,
                                    uint64_t *id);
 /* *done = 1 once the outputs are on the device at *dev_out (valid until
- * prand_server_release); *latency_s = completion time - submit time. */
+ * prand_server_release); *latency_s = completion time - submit time.
+ * Errors: PRAND_ERR_ARG (null server, unknown id). */
 prand_status_t prand_server_query(prand_server_t srv, uint64_t id, int32_t *done, void **dev_out, double *latency_s);
-/* Copy the first `bytes` of a completed request's output to host memory. */
+/* Copy the first `bytes` of a completed request's output to host memory
+ * (synchronous).  Errors: PRAND_ERR_ARG (null pointer, more bytes than the
+ * output), PRAND_ERR_STATE (unknown or unfinished id), PRAND_ERR_CUDA. */
 prand_status_t prand_server_read(prand_server_t srv, uint64_t id, void *host_dst, uint64_t bytes);
-/* Ids of requests completed since the last call (at most cap; *n = count). */
+/* Ids of requests completed since the last call (at most cap; *n = count).
+ * Errors: PRAND_ERR_ARG (null server or n, ids NULL with cap > 0). */
 prand_status_t prand_server_completed(prand_server_t srv, uint64_t *ids, size_t cap, size_t *n);
-/* Return a completed request's output memory to the arena. */
+/* Return a completed request's output memory to the arena.
+ * Errors: PRAND_ERR_ARG (null server), PRAND_ERR_STATE (unknown or unfinished id). */
 prand_status_t prand_server_release(prand_server_t srv, uint64_t id);
+/* Counters of the server so far.  Errors: PRAND_ERR_ARG (null pointer). */
 prand_status_t prand_server_stats(prand_server_t srv, prand_server_stats_t *stats);
-/* Stops the worker after the batches in flight; outstanding outputs are freed. */
+/* Stops the worker after the batches in flight; outstanding outputs are freed.
+ * srv == NULL is a no-op. */
 prand_status_t prand_server_destroy(prand_server_t srv);
 /* Open-loop load driver: submits reqs[i] (dev_out ignored) arrival_s[i] seconds
- * after the call, releases outputs as they complete, and writes each request's
- * latency; *wall_s = time until the last completion. */
+ * after the call (arrival_s ascending), releases outputs as they complete, and
+ * writes each request's latency; *wall_s = time until the last completion.
+ * Errors: PRAND_ERR_ARG (null arrays with n > 0, a request submit refuses). */
 prand_status_t prand_server_replay(prand_server_t srv, const prand_request_t *reqs, const double *arrival_s, size_t n,
                                    double *latency_s, double *wall_s);
 
