@@ -2,8 +2,9 @@
 
 Each pin is external to the oracle: the C++ standard's check value, two
 independent MT19937 implementations (numpy's legacy RandomState, CPython's
-random module), brute force (jump == single steps), and closed forms of the
-characteristic polynomial (degree 19937, x^(2^19937) = x).
+random module), brute force (jump == single steps), closed forms of the
+characteristic polynomial (degree 19937, x^(2^19937) = x), and numpy's own
+MT19937 jump by 2^128 (an independent jump implementation).
 """
 import os
 import random
@@ -43,6 +44,44 @@ def test_init_by_array_matches_cpython(seed):
     r = random.Random(seed)
     ref = np.array([r.getrandbits(32) for _ in range(3000)], dtype=np.uint32)
     assert np.array_equal(O.State("MT19937", seed).u32(3000), ref)
+
+
+def _temper(y: int) -> int:
+    y ^= y >> 11
+    y ^= (y << 7) & 0x9D2C5680
+    y ^= (y << 15) & 0xEFC60000
+    return (y ^ (y >> 18)) & 0xFFFFFFFF
+
+
+def _per_word_outputs(key, pos: int, n: int) -> np.ndarray:
+    """Outputs from an MT19937 state held in the per-word form: the 624 most
+    recent words x_k .. x_(k+623) stored cyclically from key[pos]; each output
+    first makes x_(k+624) = x_(k+397) ^ ((x_k^u | x_(k+1)^l) A) in place of x_k
+    (the recurrence of Matsumoto & Nishimura, one word at a time) and tempers it."""
+    mt = [int(v) for v in key]
+    out = np.empty(n, dtype=np.uint32)
+    i = pos % 624
+    for t in range(n):
+        y = (mt[i] & 0x80000000) | (mt[(i + 1) % 624] & 0x7FFFFFFF)
+        mt[i] = mt[(i + 397) % 624] ^ (y >> 1) ^ (0x9908B0DF if y & 1 else 0)
+        out[t] = _temper(mt[i])
+        i = (i + 1) % 624
+    return out
+
+
+@pytest.mark.parametrize("seed", [5489, 12345, 2**32 - 1])
+def test_jump_by_2_pow_128_matches_numpy(seed):
+    # numpy's MT19937.jumped() (a polynomial jump with numpy's own stored
+    # polynomial) applied to a state fresh from init_genrand (all 624 words
+    # unread) returns the state 2^128 outputs later in the per-word form at
+    # index pos; decoded that way it must continue exactly like the oracle's
+    # jump by 2^128.
+    _, key, pos, _, _ = np.random.RandomState(seed).get_state()
+    bg = np.random.MT19937()
+    bg.state = {"bit_generator": "MT19937", "state": {"key": key, "pos": pos}}
+    s = bg.jumped(1).state["state"]
+    ref = _per_word_outputs(s["key"], s["pos"], 1500)
+    assert np.array_equal(O.State("MT19937", seed).jump(2**128).u32(1500), ref)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 396, 397, 623, 624, 625, 1000, 1247, 1248, 19937, 65536 + 3, 10**6])
