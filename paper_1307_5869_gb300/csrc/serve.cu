@@ -42,8 +42,7 @@ double now_s()
 
 size_t esz(int dtype) { return dtype == PRAND_DTYPE_F64 ? 8 : 4; }
 
-// First-fit allocator over [0, cap) in 256-byte units, coalescing on release.
-// Output arena: best fit among the free blocks, found through a size-ordered
+// Output arena over [0, cap) in 256-byte units: best fit among the free blocks, found through a size-ordered
 // index (O(log n) per allocation however fragmented the arena is), and
 // neighbouring free blocks merged on release through the offset-ordered map.
 struct Arena {
