@@ -237,7 +237,7 @@ uint64_t prand_kernel_launches(void);
  * Errors: PRAND_ERR_ARG (null pointer with n > 0, unknown map), PRAND_ERR_ALIGN,
  * PRAND_ERR_CUDA (launch failure). */
 #define PRAND_MAP_MRG_F64 3
-prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out, cudaStream_t stream);
+prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out, prand_stream_t stream);
 
 /* ---- Batched requests (no counterpart in the paper: many streams of mixed
  * generators in one launch; each request is the paper's block-split stream,
@@ -431,7 +431,10 @@ double prand_chi2_sf(double x, double dof);
  * loads the library until the process exits.  n_streams above 65536 returns
  * PRAND_ERR_ARG.  The first call on a device sets that device up (looks up the
  * array addresses and fills the table with one launch it waits for), so make
- * the first call before any stream capture.  All calls share the scratch:
+ * the first call before any stream capture; a call after a device reset
+ * (cudaDeviceReset) finds a new context and repeats the set-up.  The calls
+ * after the first check the device's context and array addresses on the host
+ * (no device work, no wait).  All calls share the scratch:
  * calls that overlap on the GPU (different streams, or different host threads)
  * race and must be serialised by the caller.  Asynchronous on `stream` after
  * the first call.  Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_CUDA. */

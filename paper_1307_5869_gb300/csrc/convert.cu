@@ -30,9 +30,7 @@ __global__ void __launch_bounds__(256) convert_kernel(const uint32_t *__restrict
 template <typename OutT, bool MRG>
 prand_status_t launch(const uint32_t *in, uint64_t n, void *out, cudaStream_t st)
 {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
     const uint64_t want = (n / 4 + 255) / 256;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 8));
     const bool vec = (uintptr_t)in % 16 == 0 && (uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16) == 0;
@@ -46,8 +44,10 @@ prand_status_t launch(const uint32_t *in, uint64_t n, void *out, cudaStream_t st
 
 using namespace prand;
 
-extern "C" prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out, cudaStream_t stream)
+extern "C" prand_status_t prand_convert(const uint32_t *dev_in, uint64_t n, int32_t map, void *dev_out,
+                                        prand_stream_t stream_)
 {
+    cudaStream_t stream = (cudaStream_t)stream_;
     if ((!dev_in || !dev_out) && n) return PRAND_ERR_ARG;
     if (map != PRAND_DTYPE_F32 && map != PRAND_DTYPE_F64 && map != PRAND_MAP_MRG_F64) return PRAND_ERR_ARG;
     if (n == 0) return PRAND_OK;

@@ -82,3 +82,30 @@ def test_binding_raises_on_error(lib):
     assert P._check(7, "prand_init_streams", allow_warn=True) == 7
     with pytest.raises(ValueError):
         P.prand_skipahead(0, -1)
+
+
+def _compile_alone(tmp_path, compiler, std, header, ext):
+    import shutil
+    import subprocess
+    if not shutil.which(compiler):
+        pytest.skip(f"{compiler} not found")
+    src = tmp_path / f"only_{header.replace('.', '_')}.{ext}"
+    src.write_text(f'#include "{header}"\nint main(void) {{ return 0; }}\n')
+    res = subprocess.run([compiler, f"-std={std}", "-Wall", "-Werror", "-fsyntax-only",
+                          "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+
+
+@pytest.mark.parametrize("std", ["c99", "c11"])
+def test_prand_h_is_a_self_contained_c_header(tmp_path, std):
+    # a C translation unit that includes only prand.h must compile: every type
+    # the declarations use (streams included) comes from the header itself
+    _compile_alone(tmp_path, "gcc", std, "prand.h", "c")
+
+
+def test_prand_h_compiles_as_cpp(tmp_path):
+    _compile_alone(tmp_path, "g++", "c++17", "prand.h", "cpp")
+
+
+def test_prand_device_h_compiles_with_a_host_compiler(tmp_path):
+    _compile_alone(tmp_path, "g++", "c++17", "prand_device.h", "cpp")
