@@ -287,7 +287,7 @@ struct Engine {
     cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
     uint32_t *d_counter = nullptr;
     BatchParams params;
-    int sms = 152, blocks_per_sm[2] = { 1, 1 };  // per kernel build
+    int sms = 1, blocks_per_sm[2] = { 1, 1 };  // per kernel build (set at engine start)
     cudaStream_t aux = nullptr;                   // second branch of mixed launches
     cudaEvent_t fork = nullptr, join = nullptr;
     std::mutex aux_mu;
@@ -309,7 +309,7 @@ prand_status_t engine_get(Engine **out)
         if (s != PRAND_OK) return s;
         if (!dev_alloc(&E.d_counter, 64)) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
-        cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, dev);
+        E.sms = device_sm_count();
         for (int m = 0; m < 2; ++m) {
             int bps = 0;
             const cudaError_t e = m == kModeMt

@@ -296,8 +296,8 @@ inline uint64_t resident_threads(K kernel)
         const uint64_t c = cache[dev].load(std::memory_order_relaxed);
         if (c) return c;
     }
-    int sms = 152, bps = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
+    int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, BS, 0) != cudaSuccess || bps < 1) bps = 1;
     const uint64_t c = (uint64_t)sms * bps * BS;
     if (dev >= 0 && dev < kDevs) cache[dev].store(c, std::memory_order_relaxed);

@@ -77,6 +77,17 @@ struct GmParams {
 };
 
 inline bool is_gm(int gen) { return gen >= PRAND_GM19 && gen <= PRAND_GQ58_4; }
+
+// SM count of the current device, from the runtime (1 if the query fails: the
+// next CUDA call then reports the error).
+inline int device_sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    return sms;
+}
 const GmParams &gm_params(int gen);
 
 // Block length L as a 64-bit value for GM/GQ and the Table 4 capacity per generator.

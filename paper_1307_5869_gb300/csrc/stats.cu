@@ -272,9 +272,7 @@ __global__ void __launch_bounds__(kStitchThreads) gap_stitch_kernel(const unsign
 
 unsigned grid_for_words(uint64_t units)
 {
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
     const uint64_t want = (units + kBlock - 1) / kBlock;
     return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * 8));
 }
