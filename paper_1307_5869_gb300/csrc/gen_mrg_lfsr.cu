@@ -558,6 +558,7 @@ prand_status_t mrg_lfsr_gen(int gen, const DevTables *T, void *d_state, void *d_
 // next-state buffer used when streams are split into sections, and the jump
 // table the sections start from) lives in the file-scope device arrays below,
 // which every GPU that loads this library keeps until the process exits.
+#include <cuda.h>  // CUcontext and CUresult (the driver functions are fetched through the runtime)
 #include <mutex>
 
 namespace prand {
@@ -576,32 +577,67 @@ namespace {
 constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDev {
     bool ready = false;
-    uint32_t *next = nullptr;  // device address of g_noalloc_next on this device
-    uint32_t *tab = nullptr;   // device address of g_noalloc_tab on this device
+    unsigned long long ctx = 0;  // id of the context the table was filled in (0: unknown)
+    uint32_t *next = nullptr;    // device address of g_noalloc_next on this device
+    uint32_t *tab = nullptr;     // device address of g_noalloc_tab on this device
 };
 NoAllocDev g_noalloc_dev[kNoAllocMaxDevices];
 std::mutex g_noalloc_mu;
 
-// Once per device, with that device current: look up the device addresses of
-// the two arrays (their host-side names are only stand-ins) and fill the jump
-// table with one launch, waited for so later calls on any stream see it.
+// The unique id of the context current on this thread, or 0 if the driver
+// cannot say.  A device reset (cudaDeviceReset) replaces the primary context,
+// and the arrays' contents with it, so the set-up is redone when the id
+// changes.  The two driver functions are fetched through the runtime, so the
+// library does not link the driver library itself.
+unsigned long long current_context_id()
+{
+    typedef CUresult (*GetCurrentFn)(CUcontext *);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetIdFn)f;
+        cudaGetLastError();  // a missing entry point is not an error of the caller's next launch
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// With the device current: look up the device addresses of the two arrays
+// (their host-side names are only stand-ins; the lookup also makes the
+// device's context current on this thread) and, the first time on a device or
+// after its context was replaced, fill the jump table with one launch, waited
+// for so later calls on any stream see it.
 prand_status_t noalloc_setup(cudaStream_t st, NoAllocDev **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return PRAND_ERR_CUDA;
+    void *next = nullptr, *tab = nullptr;
+    if (cudaGetSymbolAddress(&next, g_noalloc_next) != cudaSuccess || !next) return PRAND_ERR_CUDA;
+    if (cudaGetSymbolAddress(&tab, g_noalloc_tab) != cudaSuccess || !tab) return PRAND_ERR_CUDA;
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     NoAllocDev &D = g_noalloc_dev[dev];
-    if (!D.ready) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_next) != cudaSuccess || !p) return PRAND_ERR_CUDA;
-        D.next = (uint32_t *)p;
-        p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_tab) != cudaSuccess || !p) return PRAND_ERR_CUDA;
-        D.tab = (uint32_t *)p;
+    if (!D.ready || D.ctx != ctx || D.next != next || D.tab != tab) {
+        D.ready = false;
+        D.next = (uint32_t *)next;
+        D.tab = (uint32_t *)tab;
         mrg_table_kernel<<<1, 32, 0, st>>>(D.tab);
         prand_status_t s = launch_check();
         if (s != PRAND_OK) return s;
         if (cudaStreamSynchronize(st) != cudaSuccess) return PRAND_ERR_CUDA;
+        D.ctx = ctx;
         D.ready = true;
     }
     *out = &D;
@@ -627,13 +663,21 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     if (n_per_stream == 0) return PRAND_OK;
     uint32_t nsec;
     uint64_t seclen;
-    pick_sections(n_streams, n_per_stream, resident_threads<100>(mrg_gen_kernel<uint32_t>), &nsec, &seclen);
+    // the same section choice and store form as prand_generate_u32 on a handle:
+    // staged 128-byte row stores whenever every row start is 16-byte aligned
+    pick_sections(n_streams, n_per_stream, resident_threads<1>(mrg_gen_kernel<uint32_t, true>), &nsec, &seclen);
     int vec = ((uintptr_t)dev_out % 16) == 0;
+    constexpr uint64_t E = RowFill<uint32_t>::E;
+    const bool rows = vec && n_per_stream % E == 0 && seclen % E == 0;
     const unsigned B = 256;
+    const unsigned grid = grid_for(n_streams * nsec, B);
     uint32_t *sout = nsec > 1 ? D->next : dev_state;
-    mrg_gen_kernel<uint32_t><<<grid_for(n_streams * nsec, B), B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_streams,
-                                                                          n_per_stream, nsec, seclen, dev_out, vec,
-                                                                          NoSecJumps{});
+    if (rows)
+        mrg_gen_kernel<uint32_t, true><<<grid, B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_streams, n_per_stream,
+                                                           nsec, seclen, dev_out, vec, NoSecJumps{});
+    else
+        mrg_gen_kernel<uint32_t><<<grid, B, 0, st>>>(D->tab, dev_state, sout, n_streams, n_streams, n_per_stream, nsec,
+                                                     seclen, dev_out, vec, NoSecJumps{});
     if ((s = launch_check()) != PRAND_OK) return s;
     if (nsec > 1) {
         mrg_copy_words_kernel<<<grid_for(6 * n_streams, B), B, 0, st>>>(D->next, dev_state, 6 * n_streams);

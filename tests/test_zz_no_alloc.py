@@ -46,3 +46,44 @@ def test_noalloc_rejects_too_many_streams():
     out = torch.zeros(4, dtype=torch.int32, device="cuda")
     assert L.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), 65537, out.data_ptr(), 1, None) == 1
     assert L.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), 0, out.data_ptr(), 1, None) == 1
+
+
+def test_noalloc_second_call_on_another_stream():
+    # the set-up happens once per device; a later call on a different stream
+    # (here a fresh torch stream) runs with it and still equals the handle path
+    import torch
+    P.load(build_if_missing=True)
+    n_streams, n_per = 1000, 4096
+    g = P.Generator("MRG32K3A", 77, 5, n_streams)
+    st = torch.from_numpy(_payload(g.get_state(), n_streams).view(np.int32)).cuda()
+    out = torch.empty(n_streams * n_per, dtype=torch.int32, device="cuda")
+    first = torch.cuda.current_stream()
+    P.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), n_streams, out.data_ptr(), n_per, first.cuda_stream)
+    ref = g.generate(n_per, "u32").reshape(-1)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref), "call on the current stream differs"
+    other = torch.cuda.Stream()
+    with torch.cuda.stream(other):
+        P.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), n_streams, out.data_ptr(), n_per, other.cuda_stream)
+    other.synchronize()
+    ref = g.generate(n_per, "u32").reshape(-1)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref), "call on another stream differs"
+    assert np.array_equal(st.cpu().numpy().view(np.uint32), _payload(g.get_state(), n_streams))
+    g.close()
+
+
+def test_noalloc_zero_outputs_leaves_states_unchanged():
+    import torch
+    P.load(build_if_missing=True)
+    n_streams = 64
+    g = P.Generator("MRG32K3A", 5, 0, n_streams)
+    before = _payload(g.get_state(), n_streams)
+    st = torch.from_numpy(before.view(np.int32)).cuda()
+    out = torch.full((4,), -1, dtype=torch.int32, device="cuda")
+    P.prand_mrg32k3a_generate_u32_noalloc(st.data_ptr(), n_streams, out.data_ptr(), 0,
+                                          torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy().view(np.uint32), before)
+    assert (out.cpu() == -1).all(), "a fill of zero outputs wrote to the output"
+    g.close()
