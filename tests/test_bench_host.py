@@ -32,6 +32,10 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert set(cb["per_generator_samples_per_s"]) == {"MT19937", "LFSR113", "GM61"}
+    # ms_per_step is the measured sample step, which fits the run's own time;
+    # the whole-workload time is a separate, extrapolated key
+    assert 0 < d["ms_per_step"] < 300e3 and len(d["sample_step_ms"]) == 1
+    assert d["full_step_ms_extrapolated"] > d["ms_per_step"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
