@@ -92,6 +92,8 @@ def lib():
             L.orc_gm_param.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
             L.orc_gm_matpow.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
             L.orc_gm_point_step.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p]
+            L.orc_splitmix64.argtypes = [u64p]
+            L.orc_splitmix64.restype = ctypes.c_uint64
             L.orc_gm_point_jump.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, u64p, u64p, u64p]
             _lib = L
     return _lib
@@ -188,6 +190,35 @@ def variant_info(gen, variant: int):
     if lib().orc_variant(gid(gen), variant, ctypes.byref(nmax), arr):
         return None
     return nmax.value, sum(int(arr[i]) << (64 * i) for i in range(NBIG))
+
+
+def splitmix64(seed: int, n: int) -> list:
+    """The first n outputs of SplitMix64 from the 64-bit state `seed` (the
+    generator that expands seeds into MRG32K3A, LFSR113 and GM/GQ states)."""
+    st = ctypes.c_uint64(seed)
+    return [int(lib().orc_splitmix64(ctypes.byref(st))) for _ in range(n)]
+
+
+def gm_state_raw(gen, x_prev, x) -> "State":
+    """An oracle GM/GQ state from explicit (x^(n-1), x^(n)) of each point (the
+    first s entries; the remaining slots are zero)."""
+    s = gm_param(gen, "s")
+    if len(x_prev) != s or len(x) != s:
+        raise ValueError("need one (x_prev, x) pair per point")
+    words = np.zeros(64, dtype=np.uint64)
+    words[:s] = np.array(x_prev, dtype=np.uint64)
+    words[32:32 + s] = np.array(x, dtype=np.uint64)
+    st = State(gen)
+    raw = words.tobytes()
+    assert len(raw) == st.nbytes
+    return State(gen, raw=raw)
+
+
+def gm_state_points(st: "State"):
+    """(x_prev, x) of each point of an oracle GM/GQ state."""
+    s = gm_param(st.gen, "s")
+    words = np.frombuffer(st.raw(), dtype=np.uint64)
+    return [int(v) for v in words[:s]], [int(v) for v in words[32:32 + s]]
 
 
 def gm_param(gen, name: str) -> int:

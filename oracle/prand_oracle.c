@@ -81,6 +81,9 @@ static uint64_t splitmix64(uint64_t *s)
     return z ^ (z >> 31);
 }
 
+/* One SplitMix64 output from the caller's 64-bit state (exported for its pin). */
+uint64_t orc_splitmix64(uint64_t *s) { return splitmix64(s); }
+
 static int big_bit(const uint64_t *e, int i) { return (int)((e[i >> 6] >> (i & 63)) & 1u); }
 
 static int big_nbits(const uint64_t *e)
