@@ -104,43 +104,68 @@ __device__ __forceinline__ void batch_lfsr(const BatchTile &T, const BatchCtx &C
 }
 
 // ------------------------------------------------------------------ GM / GQ tiles
+// Lane-per-point ensembles (v = 1): the warp runs one section of the tile.
+// Thread-per-stream ensembles (v = 3, 4): lane i runs section i of the tile,
+// like the MRG32K3A and LFSR113 tiles.
 template <int GEN, typename OutT>
 __device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
 {
     using P = GmT<GEN>;
-    constexpr int G = P::lanes;
-    const int grp = lane / G, li = lane % G;
-    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const uint64_t off = (uint64_t)grp * T.seclen;
-    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
-    if (len == 0) return;  // whole group
-    const bool pt = li < P::s;
     const uint64_t *tab = C.gm_tab[GEN - PRAND_GM19];
     const bool from_slot = T.flags & kTileFromSlot;
     const uint64_t *src = from_slot ? (const uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.slot
                                     : (const uint64_t *)C.base[GEN];
-    uint64_t zp = 0, zc = 0;
-    if (pt) {
-        zp = src[li] >> P::t;
-        zc = src[P::s + li] >> P::t;
-        // exponent (slot ? 0 : stream * L) + start + off, as 128 bits
+    // exponent (slot ? 0 : stream * L) + start + off, as 128 bits
+    auto exponent = [&](uint64_t off, uint64_t &lo, uint64_t &hi) {
         const uint64_t s = T.start + off;
-        uint64_t lo = s, hi = 0;
+        lo = s;
+        hi = 0;
         if (!from_slot) {
             const uint64_t klo = T.stream * P::L_, khi = __umul64hi(T.stream, P::L_);
             lo = klo + s;
             hi = khi + (lo < klo ? 1u : 0u);
         }
+    };
+    if constexpr (P::lanes == 32) {
+        const uint64_t len = min((uint64_t)T.seclen, T.len);
+        if (len == 0) return;  // whole warp
+        uint64_t zp = src[lane] >> P::t, zc = src[P::s + lane] >> P::t;
+        uint64_t lo, hi;
+        exponent(0, lo, hi);
         gm_jump128<GEN>(tab, lo, hi, zc, zp);
-    }
-    OutT *o = (OutT *)T.out + off;
-    uint32_t *myslot = reinterpret_cast<uint32_t *>(wsm) + 4 * lane;
-    if (T.flags & kTileVec) gm_generate_section<GEN, OutT, true>(zc, zp, pt, li, gmask, o, len, myslot);
-    else gm_generate_section<GEN, OutT, false>(zc, zp, pt, li, gmask, o, len, myslot);
-    if ((T.flags & kTileLast) && pt && off + len == T.len) {
-        uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
-        d[li] = gm_canon<GEN>(zp) << P::t;
-        d[P::s + li] = gm_canon<GEN>(zc) << P::t;
+        OutT *o = (OutT *)T.out;
+        uint32_t *myslot = reinterpret_cast<uint32_t *>(wsm) + 4 * lane;
+        if (T.flags & kTileVec) gm_generate_section<GEN, OutT, true>(zc, zp, lane, o, len, myslot);
+        else gm_generate_section<GEN, OutT, false>(zc, zp, lane, o, len, myslot);
+        if ((T.flags & kTileLast) && len == T.len) {
+            uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
+            d[lane] = zp << P::t;
+            d[P::s + lane] = zc << P::t;
+        }
+    } else {
+        using Z = GmZ<GEN>;
+        const uint64_t off = (uint64_t)lane * T.seclen;
+        const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
+        Z zc[P::s], zp[P::s];
+        if (len) {
+            uint64_t lo, hi;
+            exponent(off, lo, hi);
+            gmt_load<GEN>(tab, src, src + P::s, lo, hi, zc, zp);
+        } else {
+#pragma unroll
+            for (int i = 0; i < P::s; ++i) { zc[i] = 0; zp[i] = 0; }
+        }
+        OutT *o = (OutT *)T.out + off;
+        if (T.flags & kTileVec) {
+            fill_rows<OutT>([&]() { return gmt_next_word<GEN>(zc, zp); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
+                            o, len, wsm, lane);
+        } else {
+            for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(gmt_next_word<GEN>(zc, zp));
+        }
+        if ((T.flags & kTileLast) && len && off + len == T.len) {
+            uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
+            gmt_store<GEN>(zc, zp, d, d + P::s);
+        }
     }
 }
 

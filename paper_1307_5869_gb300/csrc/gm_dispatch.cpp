@@ -49,11 +49,11 @@ static const GmParams kGmHost[8] = {
     { 15, 28, (1ull << 19) - 1, 0, 1, 32, 32, P19, 6000000ull, 1000ull },
     { 4, 2, (1ull << 29) - 3, 0, 1, 32, 32, P29, 80000000ull, 100000000ull },
     { 11, 14, (1ull << 31) - 1, 0, 1, 32, 32, P31, 80000000ull, 1000000000ull },
-    { 256, 176, (1ull << 51) - 129, 4, 4, 8, 8, P51, 10000000000ull, 1000000000000000000ull },
+    { 256, 176, (1ull << 51) - 129, 4, 4, 8, 1, P51, 10000000000ull, 1000000000000000000ull },
     { 24, 74, (1ull << 61) - 1, 0, 1, 32, 32, P61, 10000000000ull, 18000000000000000000ull },
     { 8, 48, (1ull << 29) - 3, 29, 1, 32, 32, P29, 80000000ull, 100000000ull },
-    { 8, 48, (1ull << 29) - 3, 29, 3, 12, 16, P29, 80000000ull, 200000000ull },
-    { 8, 48, (1ull << 29) - 3, 29, 4, 8, 8, P29, 80000000ull, 300000000ull },
+    { 8, 48, (1ull << 29) - 3, 29, 3, 12, 1, P29, 80000000ull, 200000000ull },
+    { 8, 48, (1ull << 29) - 3, 29, 4, 8, 1, P29, 80000000ull, 300000000ull },
 };
 
 

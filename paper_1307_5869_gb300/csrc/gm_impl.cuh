@@ -2,30 +2,42 @@
 // two-dimensional torus maps x^(n) = k x^(n-1) - q x^(n-2) (mod g) (Sec. 5.1,
 // eq. (rec1), parameters of Table 2).
 //
-// GPU layout: a group of `lanes` consecutive lanes (32, 8 or 16) runs one
-// stream, one torus point per lane, so every lane does exactly one recurrence
-// step per output word.  The word is assembled across the group with a warp
-// ballot (v = 1) or a shuffle-OR tree (v = 3, 4); the group then hands word t
-// to lane (t / 4) mod lanes, which emits four words at a time as one 16-byte
-// store, so each group writes 16 * lanes contiguous bytes per round.
+// Two GPU layouts, by the bits per point v:
+//  * v = 1 (GM19, GM29, GM31, GM61, GQ58.1; 32 points per word): a warp runs
+//    one stream, one torus point per lane; each lane does one recurrence step
+//    per output word and the word is one warp ballot (lane i <-> bit i).  The
+//    warp then hands word t to lane (t / 4) mod 32, which emits four words at
+//    a time as one 16-byte store.
+//  * v = 3, 4 (GQ58.3: 12 points; GM55, GQ58.4: 8 points): one thread runs
+//    one stream section with all of its points in registers; each point's
+//    strip is extracted from one 64-bit sum by a funnel shift and placed in the
+//    word by one logic operation, so no lane waits on another.  Rows leave
+//    through the staged 128-byte row stores of the thread-per-stream
+//    generators.
 //
-// Arithmetic is exact in 64-bit integers on z = x / 2^t modulo the prime p
-// (g = 2^t p; for GM55 and GQ58.x, k and q are even, so states kept on
-// multiples of 2^t stay there and z follows the same recurrence mod p).
-// The state is stored as x = 2^t z, (x^(n-1), x^(n)) per point.
+// Arithmetic is exact on z = x / 2^t modulo the prime p (g = 2^t p; for GM55
+// and GQ58.x, k and q are even, so states kept on multiples of 2^t stay there
+// and z follows the same recurrence mod p), in 32-bit limbs written out in
+// inline PTX: the products are 32x32 -> 32 or 64-bit multiply-adds and each
+// step folds once (lazy residues, below).  The state is stored as x = 2^t z,
+// (x^(n-1), x^(n)) per point.
 //
 // Readings (the paper prints only k, q, g, v): s = 32 points for v = 1, 8 for
 // v = 4, 12 for GQ58.3 (Table 5's threads per section); point i contributes
 // floor(2^v x_i / g) at bit v*i (truncated to 32 bits); point i of the base
 // ensemble is the base pair advanced by i * D, D = nmax * L (Table 4).
 #pragma once
+#include <type_traits>
+#include <utility>
+
 #include "devcommon.cuh"
 
 namespace prand {
 
 template <int GEN>
 struct GmT;
-// k, q, p, t, v, s, lanes, prime kind, L, nmax
+// k, q, p, t, v, s, lanes per stream (32: lane per point; 1: thread per
+// stream), prime kind, L, nmax
 #define PRAND_GM_TRAITS(GEN, K, Q, PP, T, V, S, LANES, KIND, L, NMAX)                                   \
     template <>                                                                                       \
     struct GmT<GEN> {                                                                                 \
@@ -35,19 +47,23 @@ struct GmT;
 PRAND_GM_TRAITS(PRAND_GM19, 15, 28, (1ull << 19) - 1, 0, 1, 32, 32, P19, 6000000ull, 1000ull)
 PRAND_GM_TRAITS(PRAND_GM29, 4, 2, (1ull << 29) - 3, 0, 1, 32, 32, P29, 80000000ull, 100000000ull)
 PRAND_GM_TRAITS(PRAND_GM31, 11, 14, (1ull << 31) - 1, 0, 1, 32, 32, P31, 80000000ull, 1000000000ull)
-PRAND_GM_TRAITS(PRAND_GM55, 256, 176, (1ull << 51) - 129, 4, 4, 8, 8, P51, 10000000000ull, 1000000000000000000ull)
+PRAND_GM_TRAITS(PRAND_GM55, 256, 176, (1ull << 51) - 129, 4, 4, 8, 1, P51, 10000000000ull, 1000000000000000000ull)
 PRAND_GM_TRAITS(PRAND_GM61, 24, 74, (1ull << 61) - 1, 0, 1, 32, 32, P61, 10000000000ull, 18000000000000000000ull)
 PRAND_GM_TRAITS(PRAND_GQ58_1, 8, 48, (1ull << 29) - 3, 29, 1, 32, 32, P29, 80000000ull, 100000000ull)
-PRAND_GM_TRAITS(PRAND_GQ58_3, 8, 48, (1ull << 29) - 3, 29, 3, 12, 16, P29, 80000000ull, 200000000ull)
-PRAND_GM_TRAITS(PRAND_GQ58_4, 8, 48, (1ull << 29) - 3, 29, 4, 8, 8, P29, 80000000ull, 300000000ull)
+PRAND_GM_TRAITS(PRAND_GQ58_3, 8, 48, (1ull << 29) - 3, 29, 3, 12, 1, P29, 80000000ull, 200000000ull)
+PRAND_GM_TRAITS(PRAND_GQ58_4, 8, 48, (1ull << 29) - 3, 29, 4, 8, 1, P29, 80000000ull, 300000000ull)
 #undef PRAND_GM_TRAITS
+
+// Register type of a residue during generation: 32 bits when p < 2^32.
+template <int GEN>
+using GmZ = typename std::conditional<(GmT<GEN>::p < (1ull << 32)), uint32_t, uint64_t>::type;
 
 // ----------------------------------------------------------------- one step
 // z' = k z - q z_prev (mod p) with lazy residues: between steps z stays in
 // [0, p + slack) (slack below), so a step needs one fold and no final
-// comparison.  Every fold is written as S - h p (h = the bits above the prime's
-// width), which maps onto multiply-adds rather than mask/compare chains.
-// canon() returns the residue in [0, p); all lazy ranges are below 2p.
+// comparison.  Every fold is S - h p (h = the bits of S above the prime's
+// width), one multiply-add.  canon() returns the residue in [0, p); all lazy
+// ranges are below 2p.
 template <int GEN>
 __device__ __forceinline__ uint64_t gm_canon(uint64_t z)
 {
@@ -56,46 +72,109 @@ __device__ __forceinline__ uint64_t gm_canon(uint64_t z)
 }
 
 template <int GEN>
-__device__ __forceinline__ uint64_t gm_step(uint64_t zc, uint64_t zp);
+__device__ __forceinline__ GmZ<GEN> gm_step(GmZ<GEN> zc, GmZ<GEN> zp);
 
-// p = 2^19 - 1; lazy z < 2^19 + 128
+// p = 2^19 - 1; lazy z < 2^19 + 72.  S = 15 z + 28 (2p - y) = 15 z + 56 p - 28 y
+// lies in (0, 2^26); h = S >> 19 < 72 and S - h p = (S mod 2^19) + h.
 template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GM19>(uint64_t zc, uint64_t zp)
+__device__ __forceinline__ uint32_t gm_step<PRAND_GM19>(uint32_t z, uint32_t y)
 {
-    constexpr uint32_t p = (1u << 19) - 1;
-    uint32_t t = 2u * p - (uint32_t)zp;                    // = -z_prev (mod p), > 0
-    uint32_t S = 15u * (uint32_t)zc + 28u * t;             // < 2^26
-    uint32_t h = S >> 19;
-    return S - h * p;                                      // (S mod 2^19) + h < 2^19 + 128
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .u32 a, h;\n\t"
+        "mad.lo.u32 a, %2, 0xFFFFFFE4, 29360072;\n\t"   // 56 p - 28 y
+        "mad.lo.u32 a, %1, 15, a;\n\t"
+        "shr.u32 h, a, 19;\n\t"
+        "mad.lo.u32 %0, h, 0xFFF80001, a;\n\t"           // S - h (2^19 - 1)
+        "}"
+        : "=r"(r) : "r"(z), "r"(y));
+    return r;
 }
-// p = 2^29 - 3; lazy z < 2^29 + 24
+// p = 2^29 - 3; lazy z < 2^29 + 24.  S = 4 z + 3 p - 2 y lies in (2^29 - 57,
+// 2^32); h = S >> 29 <= 7 and S - h p = (S mod 2^29) + 3 h.
 template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GM29>(uint64_t zc, uint64_t zp)
+__device__ __forceinline__ uint32_t gm_step<PRAND_GM29>(uint32_t z, uint32_t y)
 {
-    constexpr uint32_t p = (1u << 29) - 3;
-    uint32_t S = 4u * (uint32_t)zc + (3u * p - 2u * (uint32_t)zp);  // 4z - 2y + 3p in (2^29 - 57, 2^32)
-    uint32_t h = S >> 29;                                  // <= 7
-    return S - h * p;                                      // (S mod 2^29) + 3h < 2^29 + 24
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .u32 a, h;\n\t"
+        "mad.lo.u32 a, %2, 0xFFFFFFFE, 1610612727;\n\t"  // 3 p - 2 y
+        "mad.lo.u32 a, %1, 4, a;\n\t"
+        "shr.u32 h, a, 29;\n\t"
+        "mad.lo.u32 %0, h, 0xE0000003, a;\n\t"           // S - h (2^29 - 3)
+        "}"
+        : "=r"(r) : "r"(z), "r"(y));
+    return r;
 }
-// p = 2^31 - 1; lazy z < 2^31 + 32
+// p = 2^31 - 1; lazy z < 2^31 + 40.  S = 11 z + 14 (2p - y) < 40 * 2^31 by two
+// wide multiply-adds; h = S >> 31 < 40 and S - h p = (S mod 2^31) + h, computed
+// in the low word (the true value is below 2^32).
 template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GM31>(uint64_t zc, uint64_t zp)
+__device__ __forceinline__ uint32_t gm_step<PRAND_GM31>(uint32_t z, uint32_t y)
 {
-    constexpr uint32_t p = (1u << 31) - 1;
-    uint32_t t = 2u * p - (uint32_t)zp;                    // (0, 2^32)
-    uint64_t S = (uint64_t)(uint32_t)zc * 11u + (uint64_t)t * 14u;  // < 2^36
-    uint32_t h = (uint32_t)(S >> 31);
-    return (uint32_t)S - h * p;                            // (S mod 2^31) + h < 2^31 + 32
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .u32 t, lo, hi, h;\n\t"
+        ".reg .u64 T, S;\n\t"
+        "sub.u32 t, 0xFFFFFFFE, %2;\n\t"                 // 2 p - y
+        "mul.wide.u32 T, t, 14;\n\t"
+        "mad.wide.u32 S, %1, 11, T;\n\t"
+        "mov.b64 {lo, hi}, S;\n\t"
+        "shf.r.wrap.b32 h, lo, hi, 31;\n\t"
+        "mad.lo.u32 %0, h, 0x80000001, lo;\n\t"          // S - h (2^31 - 1)
+        "}"
+        : "=r"(r) : "r"(z), "r"(y));
+    return r;
 }
-// p = 2^51 - 129; lazy z < 2^51 + 2^18
-template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t zc, uint64_t zp)
+// p = 2^29 - 3 (GQ58.x, z = x / 2^29); lazy z < 2^29 + 312.  S = 8 z + 48 (2p -
+// y) < 2^36; h = S >> 29 <= 104 and S - h p = (S mod 2^29) + 3 h.
+__device__ __forceinline__ uint32_t gq58_step(uint32_t z, uint32_t y)
 {
-    constexpr uint64_t p = (1ull << 51) - 129;
-    uint64_t t = 2 * p - zp;                               // (0, 2^52)
-    uint64_t S = (zc << 8) + t * 176u;                     // < 2^61
-    uint64_t h = S >> 51;                                  // < 2^10
-    return S - h * p;                                      // (S mod 2^51) + 129 h < 2^51 + 2^18
+    uint32_t r;
+    asm("{\n\t"
+        ".reg .u32 t, lo, hi, h;\n\t"
+        ".reg .u64 T, S;\n\t"
+        "sub.u32 t, 1073741818, %2;\n\t"                 // 2 p - y
+        "mul.wide.u32 T, t, 48;\n\t"
+        "mad.wide.u32 S, %1, 8, T;\n\t"
+        "mov.b64 {lo, hi}, S;\n\t"
+        "shf.r.wrap.b32 h, lo, hi, 29;\n\t"
+        "mad.lo.u32 %0, h, 0xE0000003, lo;\n\t"          // S - h (2^29 - 3)
+        "}"
+        : "=r"(r) : "r"(z), "r"(y));
+    return r;
+}
+template <>
+__device__ __forceinline__ uint32_t gm_step<PRAND_GQ58_1>(uint32_t z, uint32_t y) { return gq58_step(z, y); }
+template <>
+__device__ __forceinline__ uint32_t gm_step<PRAND_GQ58_3>(uint32_t z, uint32_t y) { return gq58_step(z, y); }
+template <>
+__device__ __forceinline__ uint32_t gm_step<PRAND_GQ58_4>(uint32_t z, uint32_t y) { return gq58_step(z, y); }
+// p = 2^51 - 129; lazy z < 2^51 + 129 * 2^10.  In 32-bit limbs: t = 2p - y
+// (< 2^52), S = 256 z + 176 t < 2^61 (low limbs by two wide multiply-adds, the
+// high word by two more), h = S >> 51 < 2^10, S - h p = (S mod 2^51) + 129 h.
+template <>
+__device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t z, uint64_t y)
+{
+    uint32_t r0, r1;
+    asm("{\n\t"
+        ".reg .u32 t0, t1, a0, a1, s1, h;\n\t"
+        ".reg .u64 T, U;\n\t"
+        "sub.cc.u32 t0, 0xFFFFFEFE, %2;\n\t"             // 2 p = 2^52 - 258
+        "subc.u32 t1, 0x000FFFFF, %3;\n\t"
+        "mul.wide.u32 T, t0, 176;\n\t"
+        "mad.wide.u32 U, %4, 256, T;\n\t"                // < 2^41
+        "mov.b64 {a0, a1}, U;\n\t"
+        "mad.lo.u32 a1, t1, 176, a1;\n\t"
+        "mad.lo.u32 s1, %5, 256, a1;\n\t"                // high word of S, < 2^29
+        "shr.u32 h, s1, 19;\n\t"
+        "mad.lo.cc.u32 %0, h, 129, a0;\n\t"
+        "and.b32 s1, s1, 0x7FFFF;\n\t"
+        "addc.u32 %1, s1, 0;\n\t"
+        "}"
+        : "=r"(r0), "=r"(r1)
+        : "r"((uint32_t)y), "r"((uint32_t)(y >> 32)), "r"((uint32_t)z), "r"((uint32_t)(z >> 32)));
+    return ((uint64_t)r1 << 32) | r0;
 }
 // p = 2^61 - 1.  Generation runs on u = (2 z mod p) + 1 rather than on z.
 // Doubling modulo a Mersenne prime rotates the 61-bit residue left by one bit,
@@ -151,49 +230,50 @@ __device__ __forceinline__ bool gm61_step(uint64_t &uc, uint64_t &up)
     uc = ((uint64_t)r1 << 32) | r0;
     return (((r0 << 29) ^ ~r1) & 0x20000000u) != 0;
 }
-// p = 2^29 - 3 (GQ58.x, z = x / 2^29); lazy z < 2^29 + 384
-template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_1>(uint64_t zc, uint64_t zp)
-{
-    constexpr uint32_t p = (1u << 29) - 3;
-    uint32_t t = 2u * p - (uint32_t)zp;                    // (0, 2^30)
-    uint64_t S = (uint64_t)(uint32_t)zc * 8u + (uint64_t)t * 48u;  // < 2^36
-    uint32_t h = (uint32_t)(S >> 29);                      // < 2^7
-    return (uint32_t)S - h * p;                            // (S mod 2^29) + 3h < 2^29 + 384
-}
-template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_3>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
-template <>
-__device__ __forceinline__ uint64_t gm_step<PRAND_GQ58_4>(uint64_t zc, uint64_t zp) { return gm_step<PRAND_GQ58_1>(zc, zp); }
 
 // ----------------------------------------------------------------- strips
 // floor(2^v z / p) of the canonical residue = floor(2^v x / g): the strip of the
 // torus the point lies in, evaluated on the lazy value z.
 template <int GEN>
-__device__ __forceinline__ bool gm_strip1(uint64_t z)  // v = 1, p < 2^32: canonical z in [(p+1)/2, p)
+__device__ __forceinline__ bool gm_strip1(uint32_t z)  // v = 1, p < 2^32: canonical z in [(p+1)/2, p)
 {
     using P = GmT<GEN>;
     constexpr uint32_t half = (uint32_t)((P::p + 1) / 2);
-    return (uint32_t)z - half < (uint32_t)(P::p - half);
+    return z - half < (uint32_t)(P::p - half);
 }
 
-template <int GEN>
-__device__ __forceinline__ uint32_t gm_strip(uint64_t z)  // v = 3, 4
+// v = 3, 4: the strip of point I placed at bit v I of the word w.  For
+// p = 2^b - c, 2^v z = q0 2^b + r0 with q0 = z >> (b - v), and
+// floor(2^v z / p) = q0 + [r0 + c q0 >= p] = (2^v z + c q0 + c) >> b, one
+// 64-bit multiply-add; its low v bits are taken by a funnel shift that moves
+// bit b to bit v I, and a mask.  A lazy z in [p, p + slack) gives 2^v, whose
+// low v bits are 0, the strip of z - p.  Bits beyond 31 are dropped (GQ58.3's
+// point 10 keeps 2 of its 3 bits, point 11 none).
+template <int GEN, int I>
+__device__ __forceinline__ uint32_t gm_strip_insert(GmZ<GEN> z, uint32_t w)
 {
     using P = GmT<GEN>;
-    // p = 2^b - c: q0 = floor(2^v z / 2^b); floor(2^v z / p) = q0 + [r >= p] with
-    // r = 2^v z - q0 p.  A lazy z in [p, p + slack) gives 2^v, masked to 0.
-    if (P::kind == P51) {
-        constexpr uint64_t m = (1ull << 51) - 1;
-        uint64_t q0 = z >> (51 - P::v);
-        uint64_t r = ((z << P::v) & m) + 129u * q0;
-        return (uint32_t)(q0 + (r >= P::p ? 1u : 0u)) & ((1u << P::v) - 1u);
+    constexpr int v = P::v, pos = v * I;
+    if constexpr (pos >= 32) {
+        return w;
+    } else if constexpr (P::kind == P51) {
+        // p = 2^51 - 129, lazy z < 2^51 + 2^18: X = 16 z + 129 (q0 + 1) < 2^56;
+        // the strip is bits 51..54 of X, i.e. bits 19..22 of its high word
+        const uint32_t q0 = (uint32_t)(z >> 47);
+        const uint64_t X = (z << 4) + (uint64_t)(129u * q0 + 129u);
+        const uint32_t hi = (uint32_t)(X >> 32);
+        const uint32_t x = pos <= 19 ? hi >> (19 - pos) : hi << (pos - 19);
+        return (x & (15u << pos)) | w;
     } else {
-        constexpr uint32_t m = (1u << 29) - 1;
-        uint32_t zz = (uint32_t)z;
-        uint32_t q0 = zz >> (29 - P::v);
-        uint32_t r = ((zz << P::v) & m) + 3u * q0;
-        return (q0 + (r >= (uint32_t)P::p ? 1u : 0u)) & ((1u << P::v) - 1u);
+        // p = 2^29 - 3, lazy z < 2^29 + 312: X = 2^v z + 3 (q0 + 1) < 2^34
+        const uint32_t q0 = z >> (29 - v);
+        const uint64_t X = (uint64_t)z * (1u << v) + (3u * q0 + 3u);
+        const uint32_t lo = (uint32_t)X, hi = (uint32_t)(X >> 32);
+        uint32_t x;
+        if constexpr (pos <= 29) x = __funnelshift_r(lo, hi, 29 - pos);
+        else x = lo << (pos - 29);
+        constexpr uint32_t mask = pos + v <= 32 ? ((1u << v) - 1u) << pos : 0xFFFFFFFFu << pos;
+        return (x & mask) | w;
     }
 }
 
@@ -241,6 +321,32 @@ __device__ __forceinline__ void gm_jump128(const uint64_t *tab, uint64_t lo, uin
         if ((w2 >> b) & 1u) gm_apply<GEN>(tab + 4 * (128 + b), zc, zp);
 }
 
+// R = A B (2x2, row-major, mod p).
+template <int GEN>
+__device__ __forceinline__ void gm_mat_mul(uint64_t R[4], const uint64_t A[4], const uint64_t *B)
+{
+    using P = GmT<GEN>;
+    const uint64_t r0 = addmod_p<P::kind>(mulmod_p<P::kind>(A[0], B[0]), mulmod_p<P::kind>(A[1], B[2]));
+    const uint64_t r1 = addmod_p<P::kind>(mulmod_p<P::kind>(A[0], B[1]), mulmod_p<P::kind>(A[1], B[3]));
+    const uint64_t r2 = addmod_p<P::kind>(mulmod_p<P::kind>(A[2], B[0]), mulmod_p<P::kind>(A[3], B[2]));
+    const uint64_t r3 = addmod_p<P::kind>(mulmod_p<P::kind>(A[2], B[1]), mulmod_p<P::kind>(A[3], B[3]));
+    R[0] = r0; R[1] = r1; R[2] = r2; R[3] = r3;
+}
+
+// M^e mod p for the exponent (hi, lo) from the table (M^(2^b) for each set
+// bit; powers of one matrix commute, so the order of the products is free).
+template <int GEN>
+__device__ __forceinline__ void gm_matpow128(const uint64_t *tab, uint64_t lo, uint64_t hi, uint64_t R[4])
+{
+    R[0] = 1; R[1] = 0; R[2] = 0; R[3] = 1;
+#pragma unroll 1
+    for (int b = 0; b < 64; ++b)
+        if ((lo >> b) & 1u) gm_mat_mul<GEN>(R, R, tab + 4 * b);
+#pragma unroll 1
+    for (int b = 0; hi && b < 64; ++b)
+        if ((hi >> b) & 1u) gm_mat_mul<GEN>(R, R, tab + 4 * (64 + b));
+}
+
 __device__ __forceinline__ void mul64x64(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
 {
     lo = a * b;
@@ -270,15 +376,16 @@ __global__ void gm_seed_kernel(const uint64_t *tab, uint64_t *base, uint64_t see
 }
 
 // Stream j of the handle = base advanced by (first + j) * L, L of 128 bits (the
-// exponent, of up to 192 bits, is exact).  One group per stream.
+// exponent, of up to 192 bits, is exact).  One thread per point of a stream.
 template <int GEN>
 __global__ void gm_init_kernel(const uint64_t *tab, const uint64_t *base, uint64_t *state, uint64_t first, uint64_t n,
                                uint64_t llo, uint64_t lhi)
 {
     using P = GmT<GEN>;
-    uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / P::lanes;
-    int i = threadIdx.x % P::lanes;
-    if (g >= n || i >= P::s) return;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t g = tid / P::s;
+    const int i = (int)(tid % P::s);
+    if (g >= n) return;
     uint64_t zp = base[i] >> P::t, zc = base[P::s + i] >> P::t;
     const uint64_t k = first + g;
     uint64_t e0, c0, e1, c1;
@@ -295,9 +402,10 @@ template <int GEN>
 __global__ void gm_skip_kernel(const uint64_t *tab, uint64_t *state, uint64_t n, U256 off)
 {
     using P = GmT<GEN>;
-    uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / P::lanes;
-    int i = threadIdx.x % P::lanes;
-    if (g >= n || i >= P::s) return;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t g = tid / P::s;
+    const int i = (int)(tid % P::s);
+    if (g >= n) return;
     uint64_t zp = state[g * P::s + i] >> P::t, zc = state[(n + g) * P::s + i] >> P::t;
 #pragma unroll 1
     for (int b = 0; b < kJumpBits; ++b)
@@ -307,51 +415,49 @@ __global__ void gm_skip_kernel(const uint64_t *tab, uint64_t *state, uint64_t n,
 }
 
 // ----------------------------------------------------------------- generation
-// One step of the lane's point and the group's output word (all lanes of the
-// group end with it): a ballot for v = 1 (lane i <-> bit i), an OR-reduction
-// over the group's lanes for v = 3, 4.
+// Lane per point (v = 1): one step of the lane's point and the warp's output
+// word (lane i <-> bit i), which every lane ends with.
 template <int GEN>
-__device__ __forceinline__ uint32_t gm_next_word(uint64_t &zc, uint64_t &zp, bool pt, int li, unsigned gmask)
+__device__ __forceinline__ uint32_t gm_next_word(GmZ<GEN> &zc, GmZ<GEN> &zp)
 {
-    using P = GmT<GEN>;
+    static_assert(GmT<GEN>::lanes == 32 && GmT<GEN>::s == 32, "lane-per-point ensembles have 32 points");
     if constexpr (GEN == PRAND_GM61) {  // (zc, zp) hold the rotated values u
-        const bool b = gm61_step(zc, zp);
-        return __ballot_sync(gmask, pt && b);
+        return __ballot_sync(kFull, gm61_step(zc, zp));
     } else {
-        const uint64_t zn = gm_step<GEN>(zc, zp);
+        const GmZ<GEN> zn = gm_step<GEN>(zc, zp);
         zp = zc;
         zc = zn;
-        if (P::v == 1) return __ballot_sync(gmask, pt && gm_strip1<GEN>(zn));
-        const uint32_t w = (pt && P::v * li < 32) ? (gm_strip<GEN>(zn) << (P::v * li)) : 0u;
-        return __reduce_or_sync(gmask, w);
+        return __ballot_sync(kFull, gm_strip1<GEN>(zn));
     }
 }
 
-// One group generates `len` outputs of one section into o: rounds of 4 * lanes
-// words; lane li keeps words 4 li .. 4 li + 3 of a round and stores them
-// together, so a group writes 16 * lanes contiguous bytes per round.  The lane
-// that owns words 4c..4c+3 parks them in its own 16-byte shared-memory slot (a
-// predicated store instead of four register selects).  Full rounds run without
-// bounds checks; the last, partial round steps exactly the remaining count, so
-// every point takes exactly `len` steps.  VEC: o is 16-byte aligned (32 for
-// doubles) at every round start, so full rounds leave as one vector store per
-// lane; the two store forms are separate instantiations (a run-time branch
-// between two stores of the same values to the same addresses may be folded
-// into the wider one).
+// One warp generates `len` outputs of one section into o: rounds of 128 words;
+// lane li keeps words 4 li .. 4 li + 3 of a round and stores them together, so
+// the warp writes 512 contiguous bytes per round.  The lane that owns words
+// 4c..4c+3 parks them in its own 16-byte shared-memory slot (a predicated store
+// instead of four register selects).  Full rounds run without bounds checks;
+// the last, partial round steps exactly the remaining count, so every point
+// takes exactly `len` steps.  VEC: o is 16-byte aligned (32 for doubles) at
+// every round start, so full rounds leave as one vector store per lane; the two
+// store forms are separate instantiations (a run-time branch between two
+// stores of the same values to the same addresses may be folded into the wider
+// one).  zc, zp: the lane's point, canonical on entry and on return.
 template <int GEN, typename OutT, bool VEC>
-__device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, bool pt, int li, unsigned gmask,
-                                                    OutT *o, uint64_t len, uint32_t *myslot)
+__device__ __forceinline__ void gm_generate_section(uint64_t &zc64, uint64_t &zp64, int li, OutT *o, uint64_t len,
+                                                    uint32_t *myslot)
 {
-    constexpr int G = GmT<GEN>::lanes;
-    if constexpr (GEN == PRAND_GM61) { zc = gm61_enter(zc); zp = gm61_enter(zp); }
+    constexpr int G = 32;
+    GmZ<GEN> zc, zp;
+    if constexpr (GEN == PRAND_GM61) { zc = gm61_enter(zc64); zp = gm61_enter(zp64); }
+    else { zc = (GmZ<GEN>)zc64; zp = (GmZ<GEN>)zp64; }
     const uint64_t full = len / (4 * G);
     for (uint64_t r = 0; r < full; ++r) {
-#pragma unroll (GEN == PRAND_GM61 ? 4 : 2)
+#pragma unroll 4
         for (int c = 0; c < G; ++c) {
-            const uint32_t a = gm_next_word<GEN>(zc, zp, pt, li, gmask);
-            const uint32_t b = gm_next_word<GEN>(zc, zp, pt, li, gmask);
-            const uint32_t d = gm_next_word<GEN>(zc, zp, pt, li, gmask);
-            const uint32_t e = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            const uint32_t a = gm_next_word<GEN>(zc, zp);
+            const uint32_t b = gm_next_word<GEN>(zc, zp);
+            const uint32_t d = gm_next_word<GEN>(zc, zp);
+            const uint32_t e = gm_next_word<GEN>(zc, zp);
             if (c == li) *reinterpret_cast<uint4 *>(myslot) = make_uint4(a, b, d, e);
         }
         const uint4 wv = *reinterpret_cast<const uint4 *>(myslot);
@@ -366,7 +472,7 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, 
     if (rem) {
         uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
         for (uint32_t k = 0; k < rem; ++k) {
-            const uint32_t w = gm_next_word<GEN>(zc, zp, pt, li, gmask);
+            const uint32_t w = gm_next_word<GEN>(zc, zp);
             if ((k >> 2) == (uint32_t)li) {
                 const uint32_t u = k & 3u;
                 w0 = u == 0 ? w : w0; w1 = u == 1 ? w : w1; w2 = u == 2 ? w : w2; w3 = u == 3 ? w : w3;
@@ -379,13 +485,14 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc, uint64_t &zp, 
         if (pos + 2 < rem) q[2] = Cvt<OutT>::f(w2);
         if (pos + 3 < rem) q[3] = Cvt<OutT>::f(w3);
     }
-    if constexpr (GEN == PRAND_GM61) { zc = gm61_leave(zc); zp = gm61_leave(zp); }
+    if constexpr (GEN == PRAND_GM61) { zc64 = gm61_leave(zc); zp64 = gm61_leave(zp); }
+    else { zc64 = gm_canon<GEN>(zc); zp64 = gm_canon<GEN>(zp); }
 }
 
-// One group = one section of one stream.  The group of the last section holds
+// One warp = one section of one stream.  The warp of the last section holds
 // the stream's next state and writes it to state_out (a separate buffer when a
-// stream is split into several sections, so no group reads a state another
-// group has already replaced).
+// stream is split into several sections, so no warp reads a state another
+// warp has already replaced).
 template <int GEN, typename OutT, bool VEC>
 __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
                                                      uint64_t *state_out, uint64_t nstreams, uint64_t stride,
@@ -393,28 +500,113 @@ __global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict_
                                                      OutT *__restrict__ out)
 {
     using P = GmT<GEN>;
-    constexpr int G = P::lanes;
     __shared__ __align__(16) uint32_t slots[256 * 4];
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int li = threadIdx.x % G;
-    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1)));
-    if (gid >= nstreams * nsec) return;  // gid is uniform within a group
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int li = threadIdx.x % 32;
+    if (gid >= nstreams * nsec) return;  // gid is uniform within a warp
     const uint64_t j = gid % nstreams;
     const uint64_t start = (gid / nstreams) * seclen;
     if (start >= nper) return;
     const uint64_t len = min(seclen, nper - start);
-    const bool pt = li < P::s;
-    uint64_t zp = 0, zc = 0;
-    if (pt) {
-        zp = state_in[j * P::s + li] >> P::t;
-        zc = state_in[(stride + j) * P::s + li] >> P::t;
-        if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
+    uint64_t zp = state_in[j * P::s + li] >> P::t;
+    uint64_t zc = state_in[(stride + j) * P::s + li] >> P::t;
+    if (start) gm_jump128<GEN>(tab, start, 0, zc, zp);
+    gm_generate_section<GEN, OutT, VEC>(zc, zp, li, out + j * nper + start, len, slots + 4 * threadIdx.x);
+    if (start + len == nper) {
+        state_out[j * P::s + li] = zp << P::t;
+        state_out[(stride + j) * P::s + li] = zc << P::t;
     }
-    gm_generate_section<GEN, OutT, VEC>(zc, zp, pt, li, gmask, out + j * nper + start, len, slots + 4 * threadIdx.x);
-    if (pt && start + len == nper) {
-        state_out[j * P::s + li] = gm_canon<GEN>(zp) << P::t;
-        state_out[(stride + j) * P::s + li] = gm_canon<GEN>(zc) << P::t;
+}
+
+// Thread per stream (v = 3, 4): every point of the thread's stream takes one
+// step per output word; point I's strip goes to bit v I.
+template <int GEN, int I>
+__device__ __forceinline__ uint32_t gmt_point(GmZ<GEN> &zc, GmZ<GEN> &zp, uint32_t w)
+{
+    const GmZ<GEN> zn = gm_step<GEN>(zc, zp);
+    zp = zc;
+    zc = zn;
+    return gm_strip_insert<GEN, I>(zn, w);
+}
+template <int GEN, int... I>
+__device__ __forceinline__ uint32_t gmt_word(GmZ<GEN> *zc, GmZ<GEN> *zp, std::integer_sequence<int, I...>)
+{
+    uint32_t w = 0;
+    ((w = gmt_point<GEN, I>(zc[I], zp[I], w)), ...);
+    return w;
+}
+template <int GEN>
+__device__ __forceinline__ uint32_t gmt_next_word(GmZ<GEN> *zc, GmZ<GEN> *zp)
+{
+    return gmt_word<GEN>(zc, zp, std::make_integer_sequence<int, GmT<GEN>::s>{});
+}
+
+// Load one stream's points (x >> t) from xp, xc and advance them by the
+// exponent (hi, lo) with one matrix M^e applied to every point; canonical
+// residues in and out.
+template <int GEN>
+__device__ __forceinline__ void gmt_load(const uint64_t *tab, const uint64_t *xp, const uint64_t *xc, uint64_t lo,
+                                         uint64_t hi, GmZ<GEN> *zc, GmZ<GEN> *zp)
+{
+    using P = GmT<GEN>;
+    uint64_t c[P::s], q[P::s];
+#pragma unroll
+    for (int i = 0; i < P::s; ++i) { q[i] = xp[i] >> P::t; c[i] = xc[i] >> P::t; }
+    if (lo | hi) {
+        uint64_t M[4];
+        gm_matpow128<GEN>(tab, lo, hi, M);
+#pragma unroll
+        for (int i = 0; i < P::s; ++i) gm_apply<GEN>(M, c[i], q[i]);
     }
+#pragma unroll
+    for (int i = 0; i < P::s; ++i) { zc[i] = (GmZ<GEN>)c[i]; zp[i] = (GmZ<GEN>)q[i]; }
+}
+
+template <int GEN>
+__device__ __forceinline__ void gmt_store(const GmZ<GEN> *zc, const GmZ<GEN> *zp, uint64_t *xp, uint64_t *xc)
+{
+    using P = GmT<GEN>;
+#pragma unroll
+    for (int i = 0; i < P::s; ++i) {
+        xp[i] = gm_canon<GEN>(zp[i]) << P::t;
+        xc[i] = gm_canon<GEN>(zc[i]) << P::t;
+    }
+}
+
+// One thread = one section of one stream (sections reached by M^start).
+// ROWS: every row start is 16-byte aligned, so rows leave through the staged
+// 128-byte row stores (every lane of a warp takes part); else one store per
+// output.  The thread of the last section writes the next state to state_out.
+template <int GEN, typename OutT, bool ROWS>
+__global__ void __launch_bounds__(256) gmt_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
+                                                      uint64_t *state_out, uint64_t nstreams, uint64_t stride,
+                                                      uint64_t nper, uint32_t nsec, uint64_t seclen,
+                                                      OutT *__restrict__ out)
+{
+    using P = GmT<GEN>;
+    using Z = GmZ<GEN>;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = tid < nstreams * nsec;
+    const uint64_t j = live ? tid % nstreams : 0;
+    const uint64_t start = live ? (tid / nstreams) * seclen : 0;
+    const uint64_t len = (live && start < nper) ? min(seclen, nper - start) : 0;
+    Z zc[P::s], zp[P::s];
+    if (len) {
+        gmt_load<GEN>(tab, state_in + j * P::s, state_in + (stride + j) * P::s, start, 0, zc, zp);
+    } else {
+#pragma unroll
+        for (int i = 0; i < P::s; ++i) { zc[i] = 0; zp[i] = 0; }
+        if (!ROWS) return;
+    }
+    OutT *o = out + j * nper + start;
+    if constexpr (ROWS) {
+        __shared__ __align__(16) unsigned char tiles[256 / 32][kTileBytes];
+        fill_rows<OutT>([&]() { return gmt_next_word<GEN>(zc, zp); }, [](uint32_t u) { return Cvt<OutT>::f(u); }, o,
+                        len, tiles[threadIdx.x >> 5], threadIdx.x & 31);
+    } else {
+        for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(gmt_next_word<GEN>(zc, zp));
+    }
+    if (len && start + len == nper) gmt_store<GEN>(zc, zp, state_out + j * P::s, state_out + (stride + j) * P::s);
 }
 
 // ----------------------------------------------------------------- host side
@@ -438,25 +630,25 @@ struct GmHost {
                                const Variant &V, cudaStream_t st)
     {
         const unsigned B = 128;
-        gm_init_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, base, state, first, n, V.L[0],
-                                                                               V.L[1]);
+        gm_init_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::s, B), B, 0, st>>>(tab, base, state, first, n, V.L[0], V.L[1]);
         return launch_check();
     }
     static prand_status_t skip(const uint64_t *tab, uint64_t *state, uint64_t n, const U256 &off, cudaStream_t st)
     {
         const unsigned B = 128;
-        gm_skip_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::lanes, B), B, 0, st>>>(tab, state, n, off);
+        gm_skip_kernel<GEN><<<gm_grid_for(n * GmT<GEN>::s, B), B, 0, st>>>(tab, state, n, off);
         return launch_check();
     }
-    // Sections per stream: whole waves of the kernel's resident lane groups
-    // (cap), section starts on multiples of 4 G outputs.
+    // Sections per stream: whole waves of the kernel's resident warps (lane
+    // per point) or threads (thread per stream), cap; sections start on
+    // multiples of 128 outputs (a warp's round) or 32 outputs (a 128-byte row).
     static void pick(uint64_t nstreams, uint64_t nper, uint64_t cap, uint32_t *nsec, uint64_t *seclen)
     {
-        constexpr int G = GmT<GEN>::lanes;
-        const uint32_t s = pick_nsec(nstreams, cap, nper / (16 * G), nper);
+        constexpr uint64_t A = GmT<GEN>::lanes == 32 ? 128 : 32;
+        const uint32_t s = pick_nsec(nstreams, cap, GmT<GEN>::lanes == 32 ? nper / 512 : nper / 256, nper);
         uint64_t len = (nper + s - 1) / s;
-        len = (len + 4 * G - 1) / (4 * G) * (4 * G);
-        if (len == 0) len = 4 * G;
+        len = (len + A - 1) / A * A;
+        if (len == 0) len = A;
         *seclen = len;
         *nsec = (uint32_t)((nper + len - 1) / len);
         if (*nsec == 0) *nsec = 1;
@@ -465,21 +657,32 @@ struct GmHost {
     static prand_status_t gen(const uint64_t *tab, uint64_t *state, uint64_t *spare, StreamRange &R, OutT *out,
                               uint64_t nper, cudaStream_t st)
     {
-        constexpr int G = GmT<GEN>::lanes;
-        if (R.nsec == 0)
-            pick(R.count, nper, resident_threads<GEN>(gm_gen_kernel<GEN, OutT, true>) / G, &R.nsec, &R.seclen);
-        const uint32_t nsec = R.nsec;
-        const uint64_t seclen = R.seclen, nstreams = R.count;
-        // section starts are multiples of 4 G, so rows start 16-byte aligned when
-        // the output is aligned and n_per_stream is a multiple of 4
-        const bool vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0 && nper % 4 == 0;
+        using P = GmT<GEN>;
         const unsigned B = 256;
-        const uint64_t off = R.j0 * GmT<GEN>::s;
+        const uint64_t off = R.j0 * P::s;
         const uint64_t *sin = state + off;
-        uint64_t *sout = (nsec > 1 ? spare : state) + off;
-        const unsigned grid = gm_grid_for(nstreams * nsec * G, B);
-        if (vec) gm_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
-        else gm_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+        if constexpr (P::lanes == 32) {
+            if (R.nsec == 0) pick(R.count, nper, resident_threads<GEN>(gm_gen_kernel<GEN, OutT, true>) / 32, &R.nsec, &R.seclen);
+            const uint32_t nsec = R.nsec;
+            const uint64_t seclen = R.seclen, nstreams = R.count;
+            uint64_t *sout = (nsec > 1 ? spare : state) + off;
+            // section starts are multiples of 128, so rows start 16-byte aligned
+            // when the output is aligned and n_per_stream is a multiple of 4
+            const bool vec = ((uintptr_t)out % (sizeof(OutT) == 8 ? 32 : 16)) == 0 && nper % 4 == 0;
+            const unsigned grid = gm_grid_for(nstreams * nsec * 32, B);
+            if (vec) gm_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+            else gm_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+        } else {
+            if (R.nsec == 0) pick(R.count, nper, resident_threads<200 + GEN>(gmt_gen_kernel<GEN, OutT, true>), &R.nsec, &R.seclen);
+            const uint32_t nsec = R.nsec;
+            const uint64_t seclen = R.seclen, nstreams = R.count;
+            uint64_t *sout = (nsec > 1 ? spare : state) + off;
+            constexpr uint64_t E = RowFill<OutT>::E;
+            const bool rows = ((uintptr_t)out % 16) == 0 && nper % E == 0 && seclen % E == 0;
+            const unsigned grid = gm_grid_for(nstreams * nsec, B);
+            if (rows) gmt_gen_kernel<GEN, OutT, true><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+            else gmt_gen_kernel<GEN, OutT, false><<<grid, B, 0, st>>>(tab, sin, sout, nstreams, R.stride, nper, nsec, seclen, out);
+        }
         return launch_check();
     }
 };

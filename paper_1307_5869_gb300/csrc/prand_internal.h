@@ -70,7 +70,7 @@ struct GmParams {
     int t;             // g = 2^t p
     int v;             // output bits per point
     int s;             // points per output word
-    int lanes;         // lanes per stream group (power of two >= s)
+    int lanes;         // lanes per stream: 32 (one lane per point) or 1 (one thread per stream)
     PrimeKind kind;
     uint64_t L;        // block length (Table 4 maximal length)
     uint64_t nmax;     // number of sequences (Table 4)
