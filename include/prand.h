@@ -150,13 +150,15 @@ prand_status_t prand_generate_f64(prand_handle_t h, double *dev_out, uint64_t n_
 /* The same fills into HOST memory (the paper's host-array fill,
  * rng_generate_array_, Sec. 7.5): host_out[j * n_per_stream + i] = output i of
  * stream j, the values prand_generate_* would write.  host_out is
- * caller-owned host memory aligned to the element size; page-locked memory
- * (cudaMallocHost / cudaHostRegister) gives full copy bandwidth, pageable
- * memory works but copies more slowly.  The outputs are generated on the
- * device in blocks that fit a staging area owned by the handle (two buffers of
- * 256 MiB, or PRAND_HOST_STAGE_BYTES from the environment at the handle's first
- * host fill, allocated then and freed by prand_destroy), each block's copy
- * overlapping the next block's generation.  Generation runs on `stream`
+ * caller-owned host memory aligned to the element size.  Page-locked memory
+ * (cudaMallocHost / cudaHostAlloc / cudaHostRegister, mapped into the device's
+ * address space as every page-locked allocation is under unified addressing)
+ * is written by the generation kernels directly, over the host link, with no
+ * staging.  Pageable memory works too: its outputs are generated on the device
+ * in blocks that fit a staging area owned by the handle (two buffers of 256
+ * MiB, or PRAND_HOST_STAGE_BYTES from the environment at the handle's first
+ * pageable host fill, allocated then and freed by prand_destroy), each block's
+ * copy overlapping the next block's generation.  Generation runs on `stream`
  * (after work already queued there); the call returns once every output is in
  * host_out.
  * Errors: PRAND_ERR_ARG, PRAND_ERR_ALIGN, PRAND_ERR_STATE, PRAND_ERR_NOMEM

@@ -287,11 +287,29 @@ prand_status_t ensure_staging(prand_handle_t h)
     return PRAND_OK;
 }
 
-// The host-array fill: the outputs are generated on the device in blocks of
+// The device address of host_out when the device can write it directly: a
+// page-locked host allocation (under unified addressing every page-locked
+// allocation is mapped into the device's address space).  nullptr for
+// pageable memory, which goes through the staged copies below.
+void *mapped_host_address(void *host_out)
+{
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, host_out) != cudaSuccess) {
+        cudaGetLastError();  // an unknown pointer is not an error of a later launch
+        return nullptr;
+    }
+    return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
+}
+
+// The host-array fill.  Page-locked host_out: the generation kernels write the
+// outputs straight into it over the host link (no staging buffer, no copy
+// engine; a compute-bound generator then costs no more than its device fill).
+// Pageable host_out: the outputs are generated on the device in blocks of
 // (streams x outputs) that fit a staging buffer and copied into host_out, the
 // copy of one block overlapping the generation of the next (two buffers, two
 // streams).  Output blocks run in order; within one, the stream blocks share
-// one section split, so their next states land in the same buffer.
+// one section split, so their next states land in the same buffer.  Either
+// way the outputs are in host_out when the call returns.
 prand_status_t generate_host(prand_handle_t h, void *host_out, int dtype, uint64_t nper, prand_stream_t stream)
 {
     if (!h || !host_out) return PRAND_ERR_ARG;
@@ -303,6 +321,11 @@ prand_status_t generate_host(prand_handle_t h, void *host_out, int dtype, uint64
     uint64_t total, bytes;
     if (mul_overflows(h->n, nper, &total) || mul_overflows(total, esz, &bytes)) return PRAND_ERR_ARG;
     if (nper == 0) return PRAND_OK;
+    if (void *mapped = mapped_host_address(host_out)) {
+        s = generate_any(h, mapped, dtype, nper, stream);
+        if (s == PRAND_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) s = PRAND_ERR_CUDA;
+        return s;
+    }
     if ((s = ensure_staging(h)) != PRAND_OK) return s;
     const uint64_t n = h->n, stage = h->stage_bytes;
     // outputs per block: whole rows when 65536 streams (or all) fit, else

@@ -92,3 +92,36 @@ def test_host_fill_errors():
         assert np.all((buf >= 0) & (buf < 1))
     finally:
         P.prand_destroy(h)
+
+
+@pytest.mark.parametrize("gen", ["LFSR113", "GM55", "MT19937"])
+def test_host_fill_into_page_locked_interior_and_registered_memory(gen):
+    # page-locked memory is written by the kernels directly: an interior
+    # pointer of a page-locked allocation (4-byte but not 16-byte aligned, so
+    # the scalar store forms run on host memory) and a pageable numpy array
+    # registered with cudaHostRegister both equal a device fill
+    P.load()
+    n, nper, seed = 300, 1001, 77
+    a, b, c = (P.prand_create(gen, seed) for _ in range(3))
+    try:
+        for h in (a, b, c):
+            P.prand_init_streams(h, 5, n)
+        pinned = torch.zeros(n * nper + 8, dtype=torch.int32, pin_memory=True)
+        P.prand_generate_host_u32(a, pinned.data_ptr() + 3 * 4, nper, 0)
+        dev = torch.empty(n * nper, dtype=torch.int32, device="cuda")
+        P.prand_generate_u32(b, dev.data_ptr(), nper, 0)
+        want = dev.cpu().numpy().view(np.uint32)
+        got = pinned.numpy().view(np.uint32)
+        assert np.array_equal(got[3:3 + n * nper], want)
+        assert not got[:3].any() and not got[3 + n * nper:].any()  # nothing outside the array
+        arr = np.zeros(n * nper, dtype=np.uint32)
+        rt = torch.cuda.cudart()
+        assert int(rt.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0)) == 0
+        try:
+            P.prand_generate_host_u32(c, arr.ctypes.data, nper, 0)
+        finally:
+            rt.cudaHostUnregister(arr.ctypes.data)
+        assert np.array_equal(arr, want)
+    finally:
+        for h in (a, b, c):
+            P.prand_destroy(h)
