@@ -157,8 +157,8 @@ __device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, 
         }
         OutT *o = (OutT *)T.out + off;
         if (T.flags & kTileVec) {
-            fill_rows<OutT>([&]() { return gmt_next_word<GEN>(zc, zp); }, [](uint32_t u) { return Cvt<OutT>::f(u); },
-                            o, len, wsm, lane);
+            fill_rows<OutT, 128, true>([&]() { return gmt_next_word<GEN>(zc, zp); },
+                                       [](uint32_t u) { return Cvt<OutT>::f(u); }, o, len, wsm, lane);
         } else {
             for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(gmt_next_word<GEN>(zc, zp));
         }
@@ -232,34 +232,41 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
 }
 
 // ------------------------------------------------------------------ the persistent kernels
-// Two builds of the same loop: MT19937 tiles only (jump chains that need many
-// registers) and every other generator (far fewer registers, so about twice
-// the resident warps).  A batch's MT19937 tiles come first in its tile list.
-enum { kModeMt = 0, kModeRest = 1 };
+// Three builds of the same loop: MT19937 tiles (jump chains that need many
+// registers), the thread-per-stream GM/GQ tiles (8 or 12 points per lane, up
+// to 128 registers), and every other generator (48 registers, so many more
+// resident warps).  A batch's tiles come in that order (order_tiles).
+enum { kModeMt = 0, kModeRest = 1, kModeWide = 2 };
+constexpr int kModes = 3;
 
 template <typename OutT, int MODE>
 __device__ __forceinline__ void batch_tile(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
 {
     if constexpr (MODE == kModeMt) {
         batch_mt<OutT>(T, C, wsm, lane);
-        return;
-    }
-    switch (T.gen) {
-    case PRAND_MRG32K3A: batch_mrg<OutT>(T, C, wsm, lane); break;
-    case PRAND_LFSR113: batch_lfsr<OutT>(T, C, wsm, lane); break;
-    case PRAND_GM19: batch_gm<PRAND_GM19, OutT>(T, C, wsm, lane); break;
-    case PRAND_GM29: batch_gm<PRAND_GM29, OutT>(T, C, wsm, lane); break;
-    case PRAND_GM31: batch_gm<PRAND_GM31, OutT>(T, C, wsm, lane); break;
-    case PRAND_GM55: batch_gm<PRAND_GM55, OutT>(T, C, wsm, lane); break;
-    case PRAND_GM61: batch_gm<PRAND_GM61, OutT>(T, C, wsm, lane); break;
-    case PRAND_GQ58_1: batch_gm<PRAND_GQ58_1, OutT>(T, C, wsm, lane); break;
-    case PRAND_GQ58_3: batch_gm<PRAND_GQ58_3, OutT>(T, C, wsm, lane); break;
-    default: batch_gm<PRAND_GQ58_4, OutT>(T, C, wsm, lane); break;
+    } else if constexpr (MODE == kModeWide) {
+        switch (T.gen) {
+        case PRAND_GM55: batch_gm<PRAND_GM55, OutT>(T, C, wsm, lane); break;
+        case PRAND_GQ58_3: batch_gm<PRAND_GQ58_3, OutT>(T, C, wsm, lane); break;
+        case PRAND_GQ58_4: batch_gm<PRAND_GQ58_4, OutT>(T, C, wsm, lane); break;
+        default: break;  // not a tile of this build (the host partitions the list)
+        }
+    } else {
+        switch (T.gen) {
+        case PRAND_MRG32K3A: batch_mrg<OutT>(T, C, wsm, lane); break;
+        case PRAND_LFSR113: batch_lfsr<OutT>(T, C, wsm, lane); break;
+        case PRAND_GM19: batch_gm<PRAND_GM19, OutT>(T, C, wsm, lane); break;
+        case PRAND_GM29: batch_gm<PRAND_GM29, OutT>(T, C, wsm, lane); break;
+        case PRAND_GM31: batch_gm<PRAND_GM31, OutT>(T, C, wsm, lane); break;
+        case PRAND_GM61: batch_gm<PRAND_GM61, OutT>(T, C, wsm, lane); break;
+        case PRAND_GQ58_1: batch_gm<PRAND_GQ58_1, OutT>(T, C, wsm, lane); break;
+        default: break;  // not a tile of this build (the host partitions the list)
+        }
     }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads, (MODE == 1 ? 20 : 1)) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
+__global__ void __launch_bounds__(kBatchThreads, (MODE == kModeRest ? 20 : MODE == kModeWide ? 8 : 1)) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
                                                               uint32_t *counter, BatchCtx ctx)
 {
     __shared__ __align__(16) unsigned char smem[kBatchThreads / 32][kWarpSmem];
@@ -312,7 +319,7 @@ struct Engine {
     cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
     uint32_t *d_counter = nullptr;
     BatchParams params;
-    int sms = 1, blocks_per_sm[2] = { 1, 1 };  // per kernel build (set at engine start)
+    int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // per kernel build (set at engine start)
     cudaStream_t aux = nullptr;                   // second branch of mixed launches
     cudaEvent_t fork = nullptr, join = nullptr;
     std::mutex aux_mu;
@@ -335,10 +342,12 @@ prand_status_t engine_get(Engine **out)
         if (!dev_alloc(&E.d_counter, 64)) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
         E.sms = device_sm_count();
-        for (int m = 0; m < 2; ++m) {
+        for (int m = 0; m < kModes; ++m) {
             int bps = 0;
             const cudaError_t e = m == kModeMt
                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeMt>, kBatchThreads, 0)
+                : m == kModeWide
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeWide>, kBatchThreads, 0)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeRest>, kBatchThreads, 0);
             E.blocks_per_sm[m] = (e == cudaSuccess && bps >= 1) ? bps : 1;
         }
@@ -435,7 +444,8 @@ BatchParams batch_params()
 static uint64_t section_length(const prand_request_t &r, const BatchParams &P, uint32_t max_tiles)
 {
     const uint64_t lanes_per_tile = is_gm(r.gen) ? (uint64_t)(32 / gm_params(r.gen).lanes) : 32ull;
-    uint64_t sec = is_gm(r.gen) ? P.seclen_gm : P.seclen_mrg_lfsr;
+    // one section per warp (lane-per-point GM/GQ) or one per lane (the rest)
+    uint64_t sec = lanes_per_tile == 1 ? P.seclen_gm : P.seclen_mrg_lfsr;
     if (max_tiles) {
         const uint64_t need = (r.length + lanes_per_tile * max_tiles - 1) / (lanes_per_tile * max_tiles);
         if (need > sec) sec = (need + 127) & ~127ull;
@@ -489,10 +499,14 @@ size_t slot_words(int gen)
     return state_bytes_per_stream(gen) / 4;
 }
 
-// Longest tiles first (MT19937 jump chains are the longest).
+bool wide_tile_gen(int gen) { return is_gm(gen) && gm_params(gen).lanes == 1; }
+
+// MT19937 tiles first, then the thread-per-stream GM/GQ tiles, then the rest;
+// longest first within each part (MT19937 jump chains are the longest).
 static uint64_t tile_cost(const BatchTile &t)
 {
-    if (t.gen == PRAND_MT19937) return (1ull << 40) + t.len;
+    if (t.gen == PRAND_MT19937) return (1ull << 41) + t.len;
+    if (wide_tile_gen(t.gen)) return (1ull << 40) + t.len;
     return t.len / (t.gen == PRAND_MRG32K3A || t.gen == PRAND_LFSR113 ? 32 : 1);
 }
 
@@ -532,31 +546,47 @@ uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles)
     return n;
 }
 
-// tiles [0, nmt) are MT19937 tiles (counter[0]), the rest any other generator
-// (counter[1]).  When both kinds are present the MT19937 part runs on `aux`,
-// forked from and joined back into `st` with the two events.
-prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t *d_counter,
-                            const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork, cudaEvent_t join)
+uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt)
 {
-    if (cudaMemsetAsync(d_counter, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
+    uint32_t n = 0;
+    while (nmt + n < tiles.size() && wide_tile_gen(tiles[nmt + n].gen)) ++n;
+    return n;
+}
+
+// Tiles [0, nmt): MT19937 (counter[0]); [nmt, nmt + nwide): thread-per-stream
+// GM/GQ (counter[2]); the rest (counter[1]).  With MT19937 tiles beside others
+// the MT19937 part runs on `aux`, forked from and joined back into `st`.
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
+                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux,
+                            cudaEvent_t fork, cudaEvent_t join)
+{
+    if (cudaMemsetAsync(d_counter, 0, 3 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
     if (!ntiles) return PRAND_OK;
-    const uint32_t nrest = ntiles - nmt;
+    const uint32_t nrest = ntiles - nmt - nwide;
+    const bool forked = nmt && (nwide || nrest);
     prand_status_t s = PRAND_OK;
-    if (nmt && nrest) {
+    if (forked) {
         if (!aux || cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
             return PRAND_ERR_CUDA;
-        batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, aux>>>(d_tiles, nmt, d_counter, ctx);
+    }
+    if (nmt) {
+        batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, forked ? aux : st>>>(d_tiles, nmt,
+                                                                                               d_counter, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
-        batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles + nmt, nrest,
+    }
+    if (nwide) {
+        batch_kernel<kModeWide><<<batch_grid(nwide, kModeWide), kBatchThreads, 0, st>>>(d_tiles + nmt, nwide,
+                                                                                       d_counter + 2, ctx);
+        if ((s = launch_check()) != PRAND_OK) return s;
+    }
+    if (nrest) {
+        batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles + nmt + nwide, nrest,
                                                                                         d_counter + 1, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
-        if (cudaEventRecord(join, aux) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
-            return PRAND_ERR_CUDA;
-        return PRAND_OK;
     }
-    if (nmt) batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, st>>>(d_tiles, nmt, d_counter, ctx);
-    else batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles, nrest, d_counter + 1, ctx);
-    return launch_check();
+    if (forked && (cudaEventRecord(join, aux) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess))
+        return PRAND_ERR_CUDA;
+    return PRAND_OK;
 }
 
 prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter)
@@ -596,7 +626,7 @@ using namespace prand;
 struct prand_batch_plan_s {
     int device = -1;
     BatchTile *d_tiles = nullptr;
-    uint32_t ntiles = 0, nmt = 0;
+    uint32_t ntiles = 0, nmt = 0, nwide = 0;
     cudaStream_t aux = nullptr;  // the second branch while capturing
     cudaEvent_t fork = nullptr, join = nullptr;
     uint32_t *d_counter = nullptr;
@@ -626,8 +656,9 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
     Engine *E;
     if ((s = engine_get(&E)) != PRAND_OK) return s;
     std::lock_guard<std::mutex> lk(E->aux_mu);  // one user of the second branch at a time
-    return launch_batch(d_tiles, (uint32_t)tiles.size(), count_mt_tiles(tiles), counter, ctx, st, E->aux, E->fork,
-                        E->join);
+    const uint32_t nmt = count_mt_tiles(tiles);
+    return launch_batch(d_tiles, (uint32_t)tiles.size(), nmt, count_wide_tiles(tiles, nmt), counter, ctx, st, E->aux,
+                        E->fork, E->join);
 }
 
 prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_request_t *reqs, size_t n, uint64_t seed)
@@ -660,6 +691,7 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     if (tiles.size() > 0xFFFFFFFFull) return fail(PRAND_ERR_ARG);
     p->ntiles = (uint32_t)tiles.size();
     p->nmt = count_mt_tiles(tiles);
+    p->nwide = count_wide_tiles(tiles, p->nmt);
     if (!dev_alloc(&p->d_counter, 64)) return fail(PRAND_ERR_NOMEM);
     if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -675,7 +707,8 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     // onto the plan's second stream and joined back)
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->nmt, p->d_counter, p->ctx, cap, p->aux, p->fork, p->join);
+    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->nmt, p->nwide, p->d_counter, p->ctx, cap, p->aux,
+                                     p->fork, p->join);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     p->graph = g;

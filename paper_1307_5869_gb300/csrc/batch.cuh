@@ -54,12 +54,19 @@ size_t slot_words(int gen);  // 32-bit words per state slot
 prand_status_t upload_tiles(const std::vector<BatchTile> &tiles, cudaStream_t st, BatchTile **d_out, uint32_t **counter);
 void order_tiles(std::vector<BatchTile> &tiles);
 prand_status_t validate_requests(const prand_request_t *reqs, size_t n);
-// Tiles [0, nmt) are MT19937 tiles, the rest other generators (order_tiles
-// puts MT19937 first).  Mixed lists run the MT19937 part on `aux`, forked from
-// and joined into `st` with the two events; a list of one kind needs none.
+// A tile list runs in three parts, each a persistent launch of its own kernel
+// build: [0, nmt) MT19937 tiles (many registers, shared memory), [nmt, nmt +
+// nwide) the thread-per-stream GM/GQ tiles (GM55, GQ58.3, GQ58.4: their points
+// need more registers than the last build allows), then every other generator
+// (few registers, many resident warps).  order_tiles puts them in that order.
+// When MT19937 tiles share a list with others they run on `aux`, forked from
+// and joined into `st` with the two events; the other two parts run one after
+// the other on `st`, so a list without MT19937 tiles needs no second stream.
+bool wide_tile_gen(int gen);
 uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles);
-prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t *d_counter,
-                            const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux = nullptr,
+uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt);
+prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
+                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux = nullptr,
                             cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 }  // namespace prand

@@ -364,7 +364,10 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
         for (size_t i = 0; i < nr; ++i) F.h_done[i] = 0;
         F.cursor = 0;
     }
-    if (lane == 1) order_tiles(tiles);  // the fast lane's tiles are alike: no sort
+    // the fast lane's tiles are alike: no sort, but the thread-per-stream GM/GQ
+    // tiles go first (their kernel build runs before the rest's)
+    if (lane == 1) order_tiles(tiles);
+    else std::stable_partition(tiles.begin(), tiles.end(), [](const BatchTile &t) { return wide_tile_gen(t.gen); });
     const size_t n = tiles.size();
     if (S->error == PRAND_OK) {
         memcpy(F.h_tiles, tiles.data(), n * sizeof(BatchTile));
@@ -376,7 +379,8 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
             cudaMemsetAsync(F.counter + 4, 0, sizeof(uint32_t), F.st) != cudaSuccess ||
             cudaMemcpyAsync(F.d_tiles, F.h_tiles, n * sizeof(BatchTile), cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
             cudaMemcpyAsync(F.d_left, F.h_left, nr * 4, cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
-            launch_batch(F.d_tiles, (uint32_t)n, count_mt_tiles(tiles), F.counter, ctx, F.st) != PRAND_OK ||
+            launch_batch(F.d_tiles, (uint32_t)n, count_mt_tiles(tiles),
+                         count_wide_tiles(tiles, count_mt_tiles(tiles)), F.counter, ctx, F.st) != PRAND_OK ||
             cudaEventRecord(F.ev, F.st) != cudaSuccess)
             S->error = PRAND_ERR_CUDA;
     }
