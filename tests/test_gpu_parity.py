@@ -206,33 +206,77 @@ def test_extreme_stream_indices(gen):
         g.close()
 
 
+def _sample_streams(gen, n, rng, count=1024):
+    """Stream indices to compare at full size: the first and last streams,
+    those on both sides of every power-of-two boundary (thread blocks, warps,
+    sections of the launch grid), and random ones, `count` in all.  MT19937
+    takes runs of 64 consecutive streams (the oracle reaches a run's first
+    stream by one jump and each next one by L more)."""
+    if gen == "MT19937":
+        runs = count // 64
+        starts = {0, n - 64, n // 2 - 32}
+        while len(starts) < runs:
+            starts.add(int(rng.integers(0, n // 64)) * 64)
+        return sorted(k for a in starts for k in range(a, a + 64))
+    ks = {0, 1, 2, n - 2, n - 1}
+    b = 2
+    while b < n:
+        ks |= {b - 1, b}
+        b *= 2
+    while len(ks) < count:
+        ks.add(int(rng.integers(0, n)))
+    return sorted(ks)
+
+
+def _oracle_rows(gen, seed, ks, nper, dts):
+    """Oracle outputs of streams ks (u32 then each later dtype continuing)."""
+    out = {dt: [] for dt in dts}
+    if gen == "MT19937":
+        for a in range(0, len(ks), 64):
+            assert ks[a + 63] == ks[a] + 63
+            st = O.Streams(gen, seed, ks[a], 64)
+            for dt in dts:
+                out[dt].append(st.generate(dt, nper))
+        return {dt: np.concatenate(v) for dt, v in out.items()}
+    for k in ks:
+        st = O.State.stream(gen, seed, k)
+        for dt in dts:
+            out[dt].append(getattr(st, dt)(nper))
+    return {dt: np.stack(v) for dt, v in out.items()}
+
+
 @pytest.mark.parametrize("gen", GENS)
 def test_table4_streams_2_pow_16_by_2_pow_12_sampled(gen):
-    # all eleven generators, 2^16 block-split streams x 2^12 outputs (u32 and f32),
-    # seed 12345; sampled streams against the oracle's stream k = base + k * L
+    # all eleven generators, 2^16 block-split streams x 2^12 outputs; u32, then
+    # f32 from a fresh identical handle; seed 12345; 1024 sampled streams
+    # against the oracle's stream k = base + k * L
     import torch
     n, nper = 1 << 16, 1 << 12
-    rng = np.random.default_rng(2024)
-    sample = sorted({0, 1, 2, n - 1} | set(int(x) for x in rng.integers(0, n, 6)))
+    ks = _sample_streams(gen, n, np.random.default_rng(2024))
+    assert len(ks) >= 1024
+    ref = _oracle_rows(gen, 12345, ks, nper, ["u32"])["u32"]
+    idx = torch.tensor(ks, device="cuda")
     for dt in ("u32", "f32"):
         g = P.Generator(gen, 12345, 0, n)
         out = g.generate(nper, dt)
-        idx = torch.tensor(sample, device="cuda")
         got = _gpu(out[idx])
         g.close()
         del out
-        want = np.stack([getattr(O.State.stream(gen, 12345, k), dt)(nper) for k in sample])
+        want = ref if dt == "u32" else O.convert(ref.reshape(-1), "f32").reshape(ref.shape)
         _assert_same(got, want, dt, f"{gen} {dt} sampled")
 
 
 @pytest.mark.parametrize("gen", ["MT19937", "LFSR113", "GM61"])
 def test_bulk_2_pow_20_streams_sampled(gen):
-    # 2^20 streams x 2^10 (2^30 outputs), u32 then f32 continuing; seed from a 64-bit counter
+    # 2^20 streams x 2^10 (2^30 outputs), u32 then f32 continuing; seed from a
+    # 64-bit counter; 1024 sampled streams
     import torch
     n, nper = 1 << 20, 1 << 10
     seed = 0x9E3779B97F4A7C15
+    ks = _sample_streams(gen, n, np.random.default_rng(7))
+    assert len(ks) >= 1024
     g = P.Generator(gen, seed, 0, n)
-    idx = torch.tensor([0, 1, 777, 65536, n // 2 + 3, n - 1], device="cuda")
+    idx = torch.tensor(ks, device="cuda")
     u = g.generate(nper, "u32")
     gu = _gpu(u[idx])
     del u
@@ -240,10 +284,9 @@ def test_bulk_2_pow_20_streams_sampled(gen):
     gf = _gpu(f[idx])
     del f
     g.close()
-    for row, k in enumerate(idx.tolist()):
-        st = O.State.stream(gen, seed, k)
-        _assert_same(gu[row], st.u32(nper), "u32", f"{gen} stream {k} u32")
-        _assert_same(gf[row], st.f32(nper), "f32", f"{gen} stream {k} f32")
+    ref = _oracle_rows(gen, seed, ks, nper, ["u32", "f32"])
+    _assert_same(gu, ref["u32"], "u32", f"{gen} u32 sampled")
+    _assert_same(gf, ref["f32"], "f32", f"{gen} f32 sampled")
 
 
 def test_batch_run_mixed_requests():
