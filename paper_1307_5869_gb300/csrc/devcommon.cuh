@@ -119,8 +119,16 @@ __device__ __forceinline__ uint64_t addmod_p(uint64_t a, uint64_t b)
 }
 
 // ---------------------------------------------------------------- floats
-// f32 = (u >> 8) * 2^-24: the 24-bit integer converts exactly, the scale is a power of two.
-__device__ __forceinline__ float u32_to_f32(uint32_t u) { return __uint2float_rn(u >> 8) * 0x1p-24f; }
+// f32 = (u >> 8) * 2^-24: the 24-bit integer converts exactly, the scale is a
+// power of two.  u >> 8 is taken as the high word of u 2^24, a multiply, so the
+// integer ALU pipe (the bound of the cheapest generators) carries one
+// operation fewer.
+__device__ __forceinline__ float u32_to_f32(uint32_t u)
+{
+    uint32_t hi;
+    asm("mul.hi.u32 %0, %1, 16777216;" : "=r"(hi) : "r"(u));
+    return __uint2float_rn(hi) * 0x1p-24f;
+}
 
 // f64 = u * 2^-32, assembled from the bits (exact) to stay off the FP64 pipe.
 __device__ __forceinline__ double u32_to_f64(uint32_t u)
@@ -219,7 +227,10 @@ constexpr int kTileBytes = RowFill<uint32_t, 128>::TILE;  // per warp, 128-byte 
 // 32 lanes of the warp taking part (lanes with len 0 only help store).
 // next() returns the next 32-bit output; cvt converts it.  tile: the warp's
 // RowFill<OutT, ROWB>::TILE bytes of shared memory.
-template <typename OutT, int ROWB = 128, typename Next, typename Conv>
+// ROLL: keep the loop over a chunk's 16-byte pieces rolled (for generators
+// whose next() is long, where unrolling a whole chunk would outgrow the
+// instruction cache).
+template <typename OutT, int ROWB = 128, bool ROLL = false, typename Next, typename Conv>
 __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, uint64_t len, unsigned char *tile, int lane)
 {
     using RF = RowFill<OutT, ROWB>;
@@ -236,7 +247,7 @@ __device__ __forceinline__ void fill_rows(Next &&next, Conv &&cvt, OutT *dst, ui
         if (__all_sync(kFull, cnt == (uint32_t)K)) {
             // every lane has a whole chunk: no per-output tests, and every row
             // segment of the tile is stored whole
-#pragma unroll
+#pragma unroll (ROLL ? 1 : PIECES)
             for (int v = 0; v < PIECES; ++v) {
                 OutT vals[E];
 #pragma unroll

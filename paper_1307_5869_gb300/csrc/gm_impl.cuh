@@ -601,8 +601,9 @@ __global__ void __launch_bounds__(256) gmt_gen_kernel(const uint64_t *__restrict
     OutT *o = out + j * nper + start;
     if constexpr (ROWS) {
         __shared__ __align__(16) unsigned char tiles[256 / 32][kTileBytes];
-        fill_rows<OutT>([&]() { return gmt_next_word<GEN>(zc, zp); }, [](uint32_t u) { return Cvt<OutT>::f(u); }, o,
-                        len, tiles[threadIdx.x >> 5], threadIdx.x & 31);
+        fill_rows<OutT, 128, true>([&]() { return gmt_next_word<GEN>(zc, zp); },
+                                   [](uint32_t u) { return Cvt<OutT>::f(u); }, o, len, tiles[threadIdx.x >> 5],
+                                   threadIdx.x & 31);
     } else {
         for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(gmt_next_word<GEN>(zc, zp));
     }
