@@ -181,7 +181,7 @@ __device__ __forceinline__ uint64_t gm_step<PRAND_GM55>(uint64_t z, uint64_t y)
 // so bit 60 of z -- the output bit floor(2 z / p) -- lands on bit 0; since the
 // map is linear the doubled values obey the same recurrence, and the offset
 // turns it into u' = 24 u - 74 u_prev + 51 (mod p).  Residues stay lazy in
-// [1, 2^61 + 256): a value u >= 2^61 stands for u - p, whose bit 0 is the
+// [1, 2^61 + 2^40): a value u >= 2^61 stands for u - p, whose bit 0 is the
 // complement of u's, so the output bit is XNOR(bit 0 of u, bit 61 of u) --
 // one logic operation instead of a 64-bit range test.
 __device__ __forceinline__ uint64_t gm61_enter(uint64_t z)  // z lazy (< 2^61 + 256) -> u
@@ -190,7 +190,7 @@ __device__ __forceinline__ uint64_t gm61_enter(uint64_t z)  // z lazy (< 2^61 + 
     const uint64_t c = z >= p ? z - p : z;
     return (((c << 1) & p) | (c >> 60)) + 1;
 }
-__device__ __forceinline__ uint64_t gm61_leave(uint64_t u)  // u -> canonical z
+__device__ __forceinline__ uint64_t gm61_leave(uint64_t u)  // u (< 2p) -> canonical z
 {
     constexpr uint64_t p = (1ull << 61) - 1;
     uint64_t w = u - 1;
@@ -198,10 +198,14 @@ __device__ __forceinline__ uint64_t gm61_leave(uint64_t u)  // u -> canonical z
     return (w >> 1) | ((w & 1) << 60);
 }
 // One step on (u, u_prev) in 32-bit limbs.  With t = C - u_prev, where
-// C = 0x23E45306EB3E4530 > 2^61 + 2^12 and 74 C = 51 (mod p),
-// S = 24 u + 74 t = u' (mod p); A = 74 t0 + 24 u0, B = 74 t1 + 24 u1 + A.hi
-// (< 2^37), h = B >> 29 and S = A.lo + h + 2^32 (B mod 2^29) (mod p), which is
-// >= 1 because S > 0.  Returns the output bit of the new value.
+// C = 0x23E45306EB3E4530 > 2^61 + 2^40 and 74 C = 51 (mod p),
+// S = 24 u + 74 t = u' (mod p).  A = 74 t0 + 24 u0 (< 2^39) and
+// B = 74 t1 + 24 u1 (< 2^37) are independent 64-bit multiply-adds, so
+// S = A + 2^32 B; with h = B >> 29 and m = B mod 2^29, 2^61 = 1 (mod p) gives
+// S = A.lo + h + 2^32 (m + A.hi) (mod p), which is below 2^61 + 2^40 and at
+// least 1 (it is 0 only if S = 0, and S > 0).  Adding A.hi after the fold,
+// rather than into B, keeps every 64-bit accumulator a product's own register
+// pair.  Returns the output bit of the new value.
 __device__ __forceinline__ bool gm61_step(uint64_t &uc, uint64_t &up)
 {
     const uint32_t u0 = (uint32_t)uc, u1 = (uint32_t)(uc >> 32);
@@ -209,20 +213,19 @@ __device__ __forceinline__ bool gm61_step(uint64_t &uc, uint64_t &up)
     uint32_t r0, r1;
     asm("{\n\t"
         ".reg .u32 t0, t1, a0, a1, b0, b1, h, m;\n\t"
-        ".reg .u64 A, B, T;\n\t"
+        ".reg .u64 A, B, T, U;\n\t"
         "sub.cc.u32 t0, 0xEB3E4530, %2;\n\t"
         "subc.u32 t1, 0x23E45306, %3;\n\t"
         "mul.wide.u32 T, t0, 74;\n\t"
         "mad.wide.u32 A, %4, 24, T;\n\t"
+        "mul.wide.u32 U, t1, 74;\n\t"
+        "mad.wide.u32 B, %5, 24, U;\n\t"
         "mov.b64 {a0, a1}, A;\n\t"
-        "cvt.u64.u32 T, a1;\n\t"
-        "mad.wide.u32 T, t1, 74, T;\n\t"
-        "mad.wide.u32 B, %5, 24, T;\n\t"
         "mov.b64 {b0, b1}, B;\n\t"
         "shf.r.wrap.b32 h, b0, b1, 29;\n\t"
         "mad.lo.u32 m, h, 0xE0000000, b0;\n\t"
         "add.cc.u32 %0, a0, h;\n\t"
-        "addc.u32 %1, m, 0;\n\t"
+        "addc.u32 %1, m, a1;\n\t"
         "}"
         : "=r"(r0), "=r"(r1)
         : "r"(v0), "r"(v1), "r"(u0), "r"(u1));

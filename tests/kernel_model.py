@@ -17,7 +17,7 @@ PARAMS = {
     "GM29": (4, 2, (1 << 29) - 3, 0, 1, 32, 24),
     "GM31": (11, 14, (1 << 31) - 1, 0, 1, 32, 40),
     "GM55": (256, 176, (1 << 51) - 129, 4, 4, 8, 129 << 10),
-    "GM61": (24, 74, (1 << 61) - 1, 0, 1, 32, 256),
+    "GM61": (24, 74, (1 << 61) - 1, 0, 1, 32, 1 << 40),
     "GQ58_1": (8, 48, (1 << 29) - 3, 29, 1, 32, 312),
     "GQ58_3": (8, 48, (1 << 29) - 3, 29, 3, 12, 312),
     "GQ58_4": (8, 48, (1 << 29) - 3, 29, 4, 8, 312),
@@ -86,21 +86,22 @@ def gm61_leave(u):
 
 
 def gm61_step(u, up):
-    """The GM61 kernel step on the rotated values: (u, u_prev) -> (u', bit)."""
+    """The GM61 kernel step on the rotated values: (u, u_prev) -> (u', bit).
+    The high product B' = 74 t1 + 24 u1 is formed without the low product's
+    carry word a1, which is added after the fold."""
     u0, u1, v0, v1 = u & M32, u >> 32, up & M32, up >> 32
     d0 = 0xEB3E4530 - v0
     t0, borrow = d0 & M32, 1 if d0 < 0 else 0
     t1 = (0x23E45306 - v1 - borrow) & M32
     A = (t0 * 74 + u0 * 24) & M64
     a0, a1 = A & M32, A >> 32
-    T = (t1 * 74 + a1) & M64
-    B = (u1 * 24 + T) & M64
+    B = (u1 * 24 + t1 * 74) & M64
     b0, b1 = B & M32, B >> 32
     h = (((b1 << 32) | b0) >> 29) & M32
     m = _mad32(h, 0xE0000000, b0)
     r = a0 + h
     r0, carry = r & M32, r >> 32
-    r1 = (m + carry) & M32
+    r1 = (m + a1 + carry) & M32
     bit = ((((r0 << 29) & M32) ^ (~r1 & M32)) & 0x20000000) != 0
     return (r1 << 32) | r0, bit
 

@@ -33,10 +33,10 @@ def test_step_is_the_recurrence_and_stays_lazy(gen):
 
 def test_gm61_step_on_rotated_values():
     # u = 2 z + 1 (mod p) obeys u' = 24 u - 74 u_prev + 51; the kernel keeps u in
-    # [1, 2^61 + 256) and its output bit is floor(2 z' / p)
+    # [1, 2^61 + 2^40) and its output bit is floor(2 z' / p)
     p = KM.P61
     rng = np.random.default_rng(2)
-    lim = (1 << 61) + 256
+    lim = (1 << 61) + (1 << 40)
     us = [1, 2, p - 1, p, lim - 1] + [int(x) for x in rng.integers(1, lim, 4000, dtype=np.uint64)]
     for u, up in zip(us, us[::-1]):
         r, bit = KM.gm61_step(u, up)
