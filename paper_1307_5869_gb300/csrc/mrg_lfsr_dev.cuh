@@ -52,9 +52,10 @@ __device__ __forceinline__ void mrg_apply_bit(const uint32_t *tab, int b, uint32
 // One MRG32K3A step (x_n = a x_{n-2} - b x_{n-3} mod m1, y_n = c y_{n-1} -
 // d y_{n-3} mod m2, Sec. 5.2) on canonical residues, in 32-bit limbs:
 // t = m - v (no borrow), S = A u + B t < 2^54 by two wide multiply-adds; with
-// 2^32 = e (mod m) (e = 209 or 22853) S folds to lo + e hi (for m2 twice,
-// the second high word being below 2^6); then r < 2^32 + 2^30 is made
-// canonical as r + e [r >= m], the condition being the carry out of r + e.
+// 2^32 = e (mod m) (e = 209 or 22853) S folds to lo + e hi (for m2 twice, the
+// first fold's e hi by a wide multiply with lo added by a carry chain, the
+// second high word being below 2^6); then r < 2^32 + 2^30 is made canonical as
+// r + e [r >= m], the condition being the carry out of r + e.
 // Returns z = x_n - y_n mod m1 in [1, m1].
 __device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_t &x2,
                                              uint32_t &y0, uint32_t &y1, uint32_t &y2)
@@ -76,15 +77,16 @@ __device__ __forceinline__ uint32_t mrg_next(uint32_t &x0, uint32_t &x1, uint32_
         "}"
         : "=r"(xn) : "r"(x1), "r"(x2));
     asm("{\n\t"
-        ".reg .u32 t, lo, hi, s0, s1, p, r, c, q;\n\t"
-        ".reg .u64 T, W, S, L;\n\t"
+        ".reg .u32 t, lo, hi, s0, s1, p0, p1, p, r, c, q;\n\t"
+        ".reg .u64 T, W, P;\n\t"
         "sub.u32 t, 4294944443, %2;\n\t"
         "mul.wide.u32 T, t, 1370589;\n\t"
         "mad.wide.u32 W, %1, 527612, T;\n\t"
         "mov.b64 {lo, hi}, W;\n\t"
-        "cvt.u64.u32 L, lo;\n\t"
-        "mad.wide.u32 S, hi, 22853, L;\n\t"
-        "mov.b64 {s0, s1}, S;\n\t"
+        "mul.wide.u32 P, hi, 22853;\n\t"
+        "mov.b64 {p0, p1}, P;\n\t"
+        "add.cc.u32 s0, p0, lo;\n\t"
+        "addc.u32 s1, p1, 0;\n\t"
         "mul.lo.u32 p, s1, 22853;\n\t"
         "add.cc.u32 r, s0, p;\n\t"
         "addc.u32 c, 0, 0;\n\t"
@@ -138,19 +140,32 @@ __device__ __forceinline__ void lfsr_apply_bit(const uint32_t *tab, int b, uint3
 // The same word step with one funnel shift: the masked part, (z & mask) << S,
 // holds bits [32 - R, 32) and ((z << Q) ^ z) >> R bits [0, 32 - R) (R = P - S),
 // so the new word is the low half of the 64-bit value (z >> (32 - P) : b) >> R,
-// b = (z << Q) ^ z -- four operations instead of five.
-template <int P, int Q, int S>
+// b = (z << Q) ^ z -- four operations instead of five.  The combined step is
+// bound by the integer ALU pipe: z << Q is written as the multiply z 2^Q (the
+// multiply pipe), and with HI, z >> (32 - P) as the high word of z 2^P
+// (P <= 31), a multiply that holds the multiply pipe twice as long, so only
+// two of the four components take it.
+template <int P, int Q, int S, bool HI>
 __device__ __forceinline__ uint32_t taus_step_funnel(uint32_t z)
 {
-    return __funnelshift_r((z << Q) ^ z, z >> (32 - P), P - S);
+    uint32_t lo, hi;
+    if constexpr (HI) {
+        asm("mul.lo.u32 %0, %2, %3;\n\t"
+            "mul.hi.u32 %1, %2, %4;"
+            : "=r"(lo), "=r"(hi) : "r"(z), "n"(1u << Q), "n"(1u << P));
+    } else {
+        asm("mul.lo.u32 %0, %1, %2;" : "=r"(lo) : "r"(z), "n"(1u << Q));
+        hi = z >> (32 - P);
+    }
+    return __funnelshift_r(lo ^ z, hi, P - S);
 }
 
 __device__ __forceinline__ uint32_t lfsr_next(uint32_t &z0, uint32_t &z1, uint32_t &z2, uint32_t &z3)
 {
-    z0 = taus_step_funnel<31, 6, 18>(z0);
-    z1 = taus_step_funnel<29, 2, 2>(z1);
-    z2 = taus_step_funnel<28, 13, 7>(z2);
-    z3 = taus_step_funnel<25, 3, 13>(z3);
+    z0 = taus_step_funnel<31, 6, 18, true>(z0);
+    z1 = taus_step_funnel<29, 2, 2, false>(z1);
+    z2 = taus_step_funnel<28, 13, 7, true>(z2);
+    z3 = taus_step_funnel<25, 3, 13, false>(z3);
     return z0 ^ z1 ^ z2 ^ z3;
 }
 
