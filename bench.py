@@ -41,12 +41,13 @@ WORKLOAD = ("bulk fill: MT19937, LFSR113, GM61; 2^20 block-split streams x (2^10
 STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 16, "GM29": 32 * 16,
                "GM31": 32 * 16, "GM55": 8 * 16, "GM61": 32 * 16, "GQ58_1": 32 * 16, "GQ58_3": 12 * 16,
                "GQ58_4": 8 * 16}
-# int32 operations per torus point step of GM61 (x' = 24 x - 74 x_prev mod 2^61 - 1) on
-# 32-bit lanes: the two-limb negation of x_prev (2), four 32x32->64 multiply-adds counted as
-# two operations each (8), the Mersenne fold (high bits, low mask, two-limb add: 4), the
-# output bit (1) and the warp ballot that assembles the word (1) -- 16 per point, 32 points
-# per output word
-GM61_OPS_PER_WORD = 16 * 32
+# Algorithmic int32 operations per output word of the integer-bound generators,
+# counted from each kernel's arithmetic on 32-bit lanes (a 32x32->64 product or
+# multiply-add counts as two operations): GM/GQ = points per word x operations
+# per point step (the step, the fold, the strip and the word assembly);
+# MRG32K3A = its two component steps and the combination.
+OPS_PER_WORD = {"GM19": 32 * 8, "GM29": 32 * 7, "GM31": 32 * 10, "GM55": 8 * 26, "GM61": 32 * 16,
+                "GQ58_1": 32 * 10, "GQ58_3": 12 * 16, "GQ58_4": 8 * 16, "MRG32K3A": 27}
 # int32 lanes per SM: four schedulers, each issuing one 32-lane warp instruction per
 # cycle (the issue-slot bound of an integer kernel; the SM count and clock are
 # queried at run time)
@@ -61,6 +62,22 @@ TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 9.466e9 / 2**20, "MT19937.f32": 9.467e
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
 SERVE_OUTPUT_BYTES = 32 << 30
+
+
+def int_issue_peak(torch, device: int, sm_max_mhz):
+    """Integer issue-slot bound (T int32 ops/s): SMs of the device (queried) x
+    128 lanes x the maximum SM clock (from nvidia-smi during the run, else the
+    measured figure, else the nominal 2070 MHz)."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    src = "nvidia-smi clocks.max.sm"
+    if not sm_max_mhz:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                sm_max_mhz, src = float(json.load(f)["sm_max_mhz"]), "measured sm_max_mhz"
+        except Exception:
+            sm_max_mhz, src = 2070.0, "nominal 2070 MHz"
+    peak = sms * LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
+    return peak, f"unit counts: {sms} SMs (queried) x {LANES_PER_SM} int32 lanes x {sm_max_mhz:g} MHz ({src})"
 
 
 def _peaks():
@@ -317,16 +334,17 @@ def run_gpu(args):
 
     # ----- rooflines (per launch, live CUDA-event durations)
     hbm_peak, peak_src = _peaks()
+    clocks = clk.summary()
+    int_peak, int_src = int_issue_peak(torch, local, clocks.get("sm_max_mhz"))
+    args.int_peak = (int_peak, int_src)
     rooflines = {}
     for g in gens:
         for dt, ms in (("u32", ms_u[g]), ("f32", ms_f[g])):
             key = f"{g}.{dt}"
             if g.startswith("GM") or g.startswith("GQ"):
-                # the int32 operation count is derived for GM61 only; the other
-                # ensembles (custom runs) report their rate without a fraction
-                ops = nS * nP * GM61_OPS_PER_WORD if g == "GM61" else None
-                rooflines[key] = {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12 if ops else None,
-                                  "peak": SMS * LANES * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
+                ops = nS * nP * OPS_PER_WORD[g]
+                rooflines[key] = {"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e12,
+                                  "peak": int_peak, "unit": "Tops/s",
                                   "ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9}
             else:
                 byts = nS * nP * 4 + 2 * nS * STATE_BYTES[g]
@@ -344,8 +362,7 @@ def run_gpu(args):
     R = rooflines[dom]
     roofline = {"bound": R["bound"], "achieved": R["achieved"], "peak": R["peak"], "unit": R["unit"],
                 "frac": R["frac"], "traffic": R.get("traffic"), "kernel": dom,
-                "peak_source": ("unit counts: 152 SMs x 128 int32 lanes x 2070 MHz" if R["bound"] == "alu"
-                                else f"{peak_src} HBM copy GB/s")}
+                "peak_source": int_src if R["bound"] == "alu" else f"{peak_src} HBM copy GB/s"}
     per_gen = {g: 2 * nS * nP / ((ms_u[g] + ms_f[g]) * 1e-3) / 1e9 for g in gens}
 
     # ----- end to end: same step through host buffers (device -> pinned host copies inside)
@@ -379,11 +396,33 @@ def run_gpu(args):
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
+        # the host link's rate for context: a plain device-to-host copy of the
+        # u32 output buffer into the same page-locked array (median of 3)
+        cp = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hu.copy_(U, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            cp.append(a.elapsed_time(b))
+        d2h_gbs = U.numel() * 4 / (statistics.median(cp) * 1e-3) / 1e9
+        # the host link's rate: the faster of that copy and the fastest host
+        # fill (an HBM-bound fill into host memory runs at the link's rate);
+        # the step can be no faster than, per fill, the slower of its bytes at
+        # that rate and its device time
+        fill_bytes = nS * nP * 4
+        link_gbs = max([d2h_gbs] + [fill_bytes / (min(v) * 1e-3) / 1e9 for v in call_ms.values()])
+        bound_ms = sum(max(fill_bytes / (link_gbs * 1e9) * 1e3, ms_u[g]) + max(fill_bytes / (link_gbs * 1e9) * 1e3,
+                                                                              ms_f[g]) for g in gens)
         e2e = {"value": world * samples_step * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": len(gens) * nS * nP * 8,
-               "steps": args.e2e_steps, "api": "prand_generate_host_u32 / _f32 into page-locked host arrays",
-               "call_ms": {k: statistics.median(v) for k, v in call_ms.items()},
-               "call_ms_each": {k: [round(x, 2) for x in v] for k, v in call_ms.items()}}
+               "steps": args.e2e_steps,
+               "api": "prand_generate_host_u32 / _f32 into page-locked host arrays (written by the kernels directly)",
+               "call_ms": {k: round(statistics.median(v), 2) for k, v in call_ms.items()},
+               "slow": {k: [round(x, 1) for x in v if x > 1.5 * statistics.median(v)] for k, v in call_ms.items()},
+               "d2h_copy_gb_per_s": round(d2h_gbs, 1), "link_gb_per_s": round(link_gbs, 1),
+               "bound_gsamples_per_s": round(world * samples_step / (bound_ms * 1e-3) / 1e9, 2)}
         del hu, hf
 
     for h in handles.values():
@@ -421,7 +460,7 @@ def run_gpu(args):
             "per_generator_gsamples_per_s": per_gen,
             "init_ms": init_ms,
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "e2e": e2e,
             "table": table,
             "single_stream": single,
@@ -472,6 +511,7 @@ def run_table(P, torch, sp, args):
     bytes = outputs + state read and written; the GM/GQ fills are integer-pipe
     bound, so their HBM fraction is small by nature."""
     hbm_peak, _ = _peaks()
+    int_peak, int_src = getattr(args, "int_peak", None) or int_issue_peak(torch, torch.cuda.current_device(), None)
     stream = torch.cuda.current_stream()
     nS, nP = W.TABLE_STREAMS, W.TABLE_PER_STREAM
     U = torch.empty(nS * nP, dtype=torch.int32, device="cuda")
@@ -489,11 +529,17 @@ def run_table(P, torch, sp, args):
             byts = nS * nP * 4 + 2 * nS * STATE_BYTES[g]
             res[dt] = {"ms": ms, "gsamples_per_s": nS * nP / (ms * 1e-3) / 1e9,
                        "hbm_frac": byts / (ms * 1e-3) / 1e9 / hbm_peak}
+            if g in OPS_PER_WORD:
+                tops = nS * nP * OPS_PER_WORD[g] / (ms * 1e-3) / 1e12
+                res[dt]["int_tops"] = tops
+                res[dt]["int_frac"] = tops / int_peak
         P.prand_destroy(h)
         out[g] = res
     del U
     torch.cuda.empty_cache()
     return {"workload": "11 generators x 2^16 streams x 2^12 outputs (u32, then f32), seed 12345",
+            "int_peak_tops": int_peak, "int_peak_source": int_src,
+            "ops_per_word": {g: OPS_PER_WORD[g] for g in W.GENERATORS if g in OPS_PER_WORD},
             "generators": out}
 
 
@@ -582,12 +628,10 @@ def run_single(P, torch, sp, args):
     return {"workload": "MRG32K3A, default state, 1 stream x 2^20 outputs", **res}
 
 
-def run_batched(P, torch, sp, args):
-    """The batched workload: 10^4 requests (generator uniform over the eleven,
-    stream uniform in [0, 1e19), length floor(2^(20 U)) u32 outputs), run as one
-    persistent launch replayed from a CUDA graph, after the tile tuner; compared
-    with the same requests as per-request plain launches (bit-identical output)."""
-    reqspec = W.batched_requests(10_000, seed=7)
+def _batched_pair(P, torch, sp, reqspec, args):
+    """One request list as a graph-replayed persistent launch (after the tile
+    tuner) and as per-request launches: device times and whether the outputs
+    agree bit for bit."""
     total = sum(n for _, _, n, _ in reqspec)
     buf = torch.empty(total, dtype=torch.int32, device="cuda")
     reqs, o = [], 0
@@ -614,24 +658,34 @@ def run_batched(P, torch, sp, args):
     fused_copy = buf.clone()
     buf.zero_()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    per_ms = identical = None
     if not args.no_per_request:
+        t0 = time.perf_counter()
         P.prand_batch_run_per_request(reqs, 7, sp)
         torch.cuda.synchronize()
         per_ms = 1e3 * (time.perf_counter() - t0)
         identical = bool(torch.equal(buf, fused_copy))
-    else:
-        per_ms, identical = None, None
     del buf, fused_copy
     torch.cuda.empty_cache()
-    n_mt = sum(1 for g, _, _, _ in reqspec if g == "MT19937")
-    return {"workload": "10^4 requests, gen uniform over 11, stream uniform [0,1e19), length floor(2^(20U)) u32, seed 7",
-            "requests": len(reqspec), "outputs": total, "mt_requests": n_mt,
-            "fused_graph_ms": fused_ms, "fused_gsamples_per_s": total / (fused_ms * 1e-3) / 1e9,
-            "per_request_ms": per_ms,
-            "speedup_vs_per_request": (per_ms / fused_ms) if per_ms else None,
-            "outputs_identical": identical,
+    return {"requests": len(reqspec), "outputs": total, "fused_graph_ms": fused_ms,
+            "fused_gsamples_per_s": total / (fused_ms * 1e-3) / 1e9, "per_request_ms": per_ms,
+            "speedup_vs_per_request": (per_ms / fused_ms) if per_ms else None, "outputs_identical": identical,
             "tuned": {"seclen_mrg_lfsr": tuned[0], "seclen_gm": tuned[1], "best_ms": tuned[2], "tune_s": tune_s}}
+
+
+def run_batched(P, torch, sp, args):
+    """The batched workload: 10^4 requests (generator uniform over the eleven,
+    stream uniform in [0, 1e19), length floor(2^(20 U)) u32 outputs), run as one
+    persistent launch replayed from a CUDA graph, after the tile tuner; compared
+    with the same requests as per-request plain launches (bit-identical output;
+    both reach each stream by the same jump method).  The same comparison is
+    repeated without the MT19937 requests, whose jump chains dominate both."""
+    reqspec = W.batched_requests(10_000, seed=7)
+    res = _batched_pair(P, torch, sp, reqspec, args)
+    res["workload"] = "10^4 requests, gen uniform over 11, stream uniform [0,1e19), length floor(2^(20U)) u32, seed 7"
+    res["mt_requests"] = sum(1 for g, _, _, _ in reqspec if g == "MT19937")
+    res["without_mt19937"] = _batched_pair(P, torch, sp, [r for r in reqspec if r[0] != "MT19937"], args)
+    return res
 
 
 def run_serving(P, args):
@@ -651,11 +705,26 @@ def run_serving(P, args):
     lat_ms = sorted(1e3 * x for x in lat)
     samples = sum(n for _, _, _, n in reqs)
     pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(q * len(lat_ms)))]
+
+    def pcts(v):
+        v = sorted(v)
+        at = lambda q: round(v[min(len(v) - 1, int(q * len(v)))], 3)
+        return {"n": len(v), "p50_ms": at(0.5), "p99_ms": at(0.99), "max_ms": round(v[-1], 3)}
+
+    # where the tail comes from: latency by generator and by length (2^6-2^10,
+    # 2^10-2^14, 2^14-2^18, 2^18-2^22 outputs)
+    by_gen, by_len = {}, {}
+    for (g, _, _, n), x in zip(reqs, lat):
+        by_gen.setdefault(g, []).append(1e3 * x)
+        b = min(3, max(0, (int(n).bit_length() - 1 - 6) // 4))
+        by_len.setdefault(f"2^{6 + 4 * b}-2^{10 + 4 * b}", []).append(1e3 * x)
     return {"workload": f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g} s; gen uniform over 11, "
                         "stream uniform [0,1e19), length floor(2^(6+16U)), dtype u32/f32/f64 equiprobable",
             "requests": len(reqs), "samples": samples, "wall_s": wall,
             "gsamples_per_s": samples / wall / 1e9, "demanded_gsamples_per_s": samples / args.serve_seconds / 1e9,
             "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat_ms[-1],
+            "by_generator": {g: pcts(v) for g, v in sorted(by_gen.items())},
+            "by_length": {k: pcts(v) for k, v in sorted(by_len.items())},
             "resident_hit_rate": st["hits"] / max(1, st["hits"] + st["misses"] + st["restores"]),
             "batches": st["batches"], "spills": st["spills"]}
 
@@ -666,7 +735,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -268,7 +268,10 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
 
 /* The same requests, one ordinary stream-initialisation launch and one
  * generation launch per request (no fusion, no persistent scheduling); the
- * comparison point for prand_batch_run.  Returns after the work completes.
+ * comparison point for prand_batch_run.  Each stream is reached by the same
+ * jump method the batched launch uses (for MT19937, one window polynomial per
+ * nonzero hex digit of the stream index), so the two differ only in how the
+ * work is launched.  Returns after the work completes.
  * Errors: as prand_batch_run. */
 prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n, uint64_t seed,
                                            prand_stream_t stream);

@@ -231,6 +231,25 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
     __syncwarp();
 }
 
+// One MT19937 stream for the per-request form: stream k = base advanced by
+// k 2^432, one window polynomial per nonzero hex digit of k (the same jump the
+// batched MT19937 tiles take), by one warp.
+__global__ void __launch_bounds__(32) mt_window_init_kernel(const uint32_t *base, const uint32_t *win, uint64_t k,
+                                                            uint32_t *dst)
+{
+    __shared__ uint32_t seq[2 * kMtN];
+    const int lane = threadIdx.x;
+    bool first = true;
+    for (int i = 0; i < kMtWinPositions; ++i) {
+        const uint32_t d = (uint32_t)(k >> (4 * i)) & 15u;
+        if (!d) continue;
+        mt_apply_poly_warp(win + ((size_t)i * 16 + d) * kMtPolyWords, first ? base : dst, dst, seq, lane);
+        first = false;
+        __syncwarp();
+    }
+    if (first) mt_copy_state_warp(base, dst, lane);
+}
+
 // ------------------------------------------------------------------ the persistent kernels
 // Three builds of the same loop: MT19937 tiles (jump chains that need many
 // registers), the thread-per-stream GM/GQ tiles (8 or 12 points per lane, up
@@ -818,7 +837,9 @@ prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n
         R.stride = R.count = 1;
         uint32_t idx = kMtN;
         if (r.gen == PRAND_MT19937) {
-            s = mt_init(T, ctx.base[r.gen], a, r.stream, 1, st);
+            mt_window_init_kernel<<<1, 32, 0, st>>>((const uint32_t *)ctx.base[r.gen], ctx.mt_win, r.stream,
+                                                    (uint32_t *)a);
+            s = launch_check();
             if (s == PRAND_OK) s = mt_gen(a, 1, &idx, r.dev_out, r.dtype, r.length, st);
         } else if (is_gm(r.gen)) {
             Variant V;
