@@ -43,11 +43,13 @@ STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 1
                "GQ58_4": 8 * 16}
 # Algorithmic int32 operations per output word of the integer-bound generators,
 # counted from each kernel's arithmetic on 32-bit lanes (a 32x32->64 product or
-# multiply-add counts as two operations): GM/GQ = points per word x operations
-# per point step (the step, the fold, the strip and the word assembly);
-# MRG32K3A = its two component steps and the combination.
-OPS_PER_WORD = {"GM19": 32 * 8, "GM29": 32 * 7, "GM31": 32 * 10, "GM55": 8 * 26, "GM61": 32 * 16,
-                "GQ58_1": 32 * 10, "GQ58_3": 12 * 16, "GQ58_4": 8 * 16, "MRG32K3A": 27}
+# multiply-add counts as two operations): GM/GQ = the points' steps (the
+# recurrence and its fold), strips and word assembly; MRG32K3A = its two
+# component steps and the combination.  Per point step: GM19, GM29 7; GM31,
+# GQ58.1 10; GM61 16; GM55 20; GQ58.3, GQ58.4 13 (GQ58.3's point 11 steps
+# without a strip: 7).
+OPS_PER_WORD = {"GM19": 32 * 7, "GM29": 32 * 7, "GM31": 32 * 10, "GM55": 8 * 20, "GM61": 32 * 16,
+                "GQ58_1": 32 * 10, "GQ58_3": 11 * 13 + 7, "GQ58_4": 8 * 13, "MRG32K3A": 28}
 # int32 lanes per SM: four schedulers, each issuing one 32-lane warp instruction per
 # cycle (the issue-slot bound of an integer kernel; the SM count and clock are
 # queried at run time)
@@ -55,9 +57,9 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) per stream of one fill of 1024 outputs, from ncu
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels
 # at 2^18 streams x 2^10 outputs, scaled per stream; None for other shapes.
-TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 9.466e9 / 2**20, "MT19937.f32": 9.467e9 / 2**20,
-                           "LFSR113.u32": 4.264e9 / 2**20, "LFSR113.f32": 4.264e9 / 2**20,
-                           "GM61.u32": 5.310e9 / 2**20, "GM61.f32": 5.311e9 / 2**20}
+TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.322e9 / 2**18, "MT19937.f32": 2.319e9 / 2**18,
+                           "LFSR113.u32": 1.025e9 / 2**18, "LFSR113.f32": 1.023e9 / 2**18,
+                           "GM61.u32": 1.281e9 / 2**18, "GM61.f32": 1.279e9 / 2**18}
 # Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
