@@ -254,6 +254,32 @@ class Streams:
         return out.reshape(self.n, n_per)
 
 
+def stream_digest(gen, seed: int, first: int, count: int, n_per: int, dtypes=("u32", "f32")) -> str:
+    """BLAKE2b digest of streams first..first+count-1, each dtype's block of
+    count x n_per outputs in turn (the later dtypes continue the streams), as
+    raw little-endian bytes.  A caller holding the same outputs from elsewhere
+    hashes them the same way to compare whole blocks at once."""
+    import hashlib
+    st = Streams(gen, seed, first, count)
+    h = hashlib.blake2b(digest_size=32)
+    for dt in dtypes:
+        h.update(np.ascontiguousarray(st.generate(dt, n_per)).tobytes())
+    return h.hexdigest()
+
+
+def _digest_job(args):
+    return stream_digest(*args)
+
+
+def stream_digests(gen, seed: int, n_streams: int, n_per: int, chunk: int, dtypes=("u32", "f32"), procs=None):
+    """stream_digest of every chunk of `chunk` streams, computed by a pool of
+    processes started with spawn (safe after the parent has used a GPU)."""
+    import multiprocessing as mp
+    jobs = [(gen, seed, a, min(chunk, n_streams - a), n_per, tuple(dtypes)) for a in range(0, n_streams, chunk)]
+    with mp.get_context("spawn").Pool(procs or os.cpu_count() or 1) as pool:
+        return pool.map(_digest_job, jobs, chunksize=1)
+
+
 def mt_charpoly() -> int:
     """The MT19937 characteristic polynomial as a Python int (bit i = x^i)."""
     arr = (ctypes.c_uint64 * 313)()
