@@ -432,10 +432,11 @@ def run_gpu(args):
     del U, F
     torch.cuda.empty_cache()
 
-    table = single = study = None
+    table = single = study = host_simd = None
     if not args.no_table and rank == 0:
         table = run_table(P, torch, sp, args)
         single = run_single(P, torch, sp, args)
+        host_simd = run_host_simd(P, torch, sp, args)
     if not args.no_study and rank == 0:
         study = run_skipahead(P, torch, sp, args)
     batched = None
@@ -466,6 +467,7 @@ def run_gpu(args):
             "e2e": e2e,
             "table": table,
             "single_stream": single,
+            "host_simd": host_simd,
             "skipahead_study": study,
             "batched": batched,
             "serving": serving,
@@ -609,6 +611,40 @@ def run_skipahead(P, torch, sp, args):
                         "frequency 2^10 cells, serial 2^5 x 2^5, gap [0, 2^29) t = 48; seed 20140401",
             "generators": res, "p_outside_1e-3": suspicious, "tests_run": 3 * len(res),
             "count_kernels_2^30_words": kern}
+
+
+def run_host_simd(P, torch, sp, args):
+    """The host SIMD generators (no GPU): MT19937, LFSR113 and MRG32K3A, u32,
+    2^16 streams x 2^10 outputs from states exported from a handle, on one
+    host thread and on all of them; wall time of the call, best of 3 (the
+    paper's SSE realisations ran one core of a Xeon X5670: MT19937 2.5e8,
+    MRG32K3A 1.5e8, LFSR113 1.6e8 outputs/s, Table 6)."""
+    import numpy as np
+    n, nper = 1 << 16, 1 << 10
+    out = np.empty(n * nper, dtype=np.uint32)
+    res = {"workload": "2^16 streams x 2^10 u32 outputs per call, states exported from a handle (seed 5)",
+           "host_threads": os.cpu_count()}
+    for g in ("MT19937", "LFSR113", "MRG32K3A"):
+        h = P.prand_create(g, 5)
+        P.prand_init_streams(h, 0, n)
+        sb = P.prand_device_state_bytes(g)
+        dev = torch.empty(n * sb // 4, dtype=torch.int32, device="cuda")
+        P.prand_export_states(h, dev.data_ptr(), sp)
+        torch.cuda.synchronize()
+        P.prand_destroy(h)
+        st = dev.cpu().numpy().copy()
+        del dev
+        r = {}
+        for label, threads in (("one_thread", 1), ("all_threads", 0)):
+            best = None
+            for _ in range(3):
+                t0 = time.perf_counter()
+                P.prand_host_generate(g, P.DTYPE_U32, st.ctypes.data, n, out.ctypes.data, nper, threads)
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            r[label] = {"gsamples_per_s": n * nper / best / 1e9, "ms": 1e3 * best}
+        res[g] = r
+    return res
 
 
 def run_single(P, torch, sp, args):

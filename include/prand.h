@@ -421,6 +421,26 @@ prand_status_t prand_test_evaluate(const prand_test_t *test, uint64_t n, const u
  * arguments. */
 double prand_chi2_sf(double x, double dof);
 
+/* ---- Host SIMD generation (the paper's SSE realisations, Sec. 2 and Table 6,
+ * restated for today's host vector units; no GPU involved) ----
+ * MT19937, MRG32K3A or LFSR113 outputs of n_streams streams computed on the
+ * host: host_states holds n_streams states in the one-struct-per-stream
+ * layouts of prand_device.h (prand_mt19937_state, prand_mrg32k3a_state,
+ * prand_lfsr113_state; e.g. from prand_export_states), advanced in place by
+ * n_per_stream outputs; host_out[j * n_per_stream + i] = output i of stream j
+ * as `dtype` (PRAND_DTYPE_U32 / _F32 / _F64), the same values prand_generate_*
+ * writes for a handle holding those states.  MT19937 vectorises each stream's
+ * twist four words at a time, LFSR113 four streams per vector, MRG32K3A two
+ * streams per vector of exact double-precision products.  n_threads: host
+ * threads the streams are spread over (0: one per hardware thread).  Returns
+ * after the outputs are written.  host_states and host_out are caller-owned
+ * host memory (host_out aligned to the element size, host_states to 4 bytes).
+ * Errors: PRAND_ERR_ARG (another generator, unknown dtype, null pointer with
+ * work to do, negative n_threads, size overflow), PRAND_ERR_ALIGN,
+ * PRAND_ERR_STATE (an MT19937 state whose index exceeds 624). */
+prand_status_t prand_host_generate(prand_gen_t gen, int32_t dtype, void *host_states, uint64_t n_streams,
+                                   void *host_out, uint64_t n_per_stream, int32_t n_threads);
+
 /* No counterpart in the paper.  MRG32K3A u32 generation that allocates no
  * memory, for callers that cannot call cudaMalloc: code that owns all device
  * memory through its own allocator or a fixed budget (a framework's caching

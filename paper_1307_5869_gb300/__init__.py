@@ -40,7 +40,7 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
            "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
            "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2", "prand_init_streams_spaced",
-           "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf"]
+           "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf", "prand_host_generate"]
 
 
 class PrandError(RuntimeError):
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = False):
     L.prand_kernel_launches.restype = u64
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
     L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
+    L.prand_host_generate.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, u64, ctypes.c_void_p, u64,
+                                      ctypes.c_int32]
     L.prand_convert.argtypes = [ctypes.c_void_p, u64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     L.prand_device_state_bytes.argtypes = [ctypes.c_int]
     L.prand_device_state_bytes.restype = u64
@@ -309,6 +311,14 @@ def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out:
     """MRG32K3A u32 fill on caller-held states without any device allocation."""
     _check(load().prand_mrg32k3a_generate_u32_noalloc(dev_state, n_streams, dev_out, n_per_stream, stream),
            "prand_mrg32k3a_generate_u32_noalloc")
+
+
+def prand_host_generate(gen, dtype: int, host_states: int, n_streams: int, host_out: int, n_per_stream: int,
+                        n_threads: int = 0) -> None:
+    """MT19937 / MRG32K3A / LFSR113 outputs computed on the host's vector units
+    from states in the prand_device.h layouts (advanced in place)."""
+    _check(load().prand_host_generate(_gid(gen), dtype, host_states, n_streams, host_out, n_per_stream, n_threads),
+           "prand_host_generate")
 
 
 MAP_MRG_F64 = 3
