@@ -708,7 +708,8 @@ def _batched_pair(P, torch, sp, reqspec, args):
     return {"requests": len(reqspec), "outputs": total, "fused_graph_ms": fused_ms,
             "fused_gsamples_per_s": total / (fused_ms * 1e-3) / 1e9, "per_request_ms": per_ms,
             "speedup_vs_per_request": (per_ms / fused_ms) if per_ms else None, "outputs_identical": identical,
-            "tuned": {"seclen_mrg_lfsr": tuned[0], "seclen_gm": tuned[1], "best_ms": tuned[2], "tune_s": tune_s}}
+            "tuned": {"seclen_mrg_lfsr": tuned[0], "seclen_gm": tuned[1], "block": tuned[2], "row_bytes": tuned[3],
+                      "best_ms": tuned[4], "tune_s": tune_s}}
 
 
 def run_batched(P, torch, sp, args):

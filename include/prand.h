@@ -286,15 +286,29 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *plan, const prand_req
 prand_status_t prand_batch_plan_launch(prand_batch_plan_t plan, prand_stream_t stream);
 prand_status_t prand_batch_plan_destroy(prand_batch_plan_t plan);
 
-/* Tile tuner (no counterpart in the paper): times the batch for each
- * candidate section length (outputs per lane for MRG32K3A/LFSR113, per lane
- * group for GM/GQ), keeps the fastest for later batches on this device, and
- * reports it (any output pointer may be NULL).  If the environment variable
+/* Tile tuner (no counterpart in the paper): times the batch (as a graph
+ * plan, mean of three launches) over the launch parameters and keeps the
+ * fastest for later batches on this device: first the two section lengths
+ * (outputs per lane of the thread-per-section tiles -- MRG32K3A, LFSR113 and
+ * the thread-per-stream GM/GQ ensembles -- and outputs per warp of the
+ * lane-per-point GM/GQ tiles: 2048, 8192 or 32768 each), then, at the best
+ * lengths, the threads per block (64 or 128) and the staged row size (128 or
+ * 256 bytes, i.e. 32 or 64 u32 outputs per row store) of the kernel build
+ * that runs MRG32K3A, LFSR113 and the lane-per-point GM/GQ tiles.  Reports the
+ * choice (any output pointer may be NULL).  If the environment variable
  * PRAND_TUNE_CACHE names a file, the result is written there and read back by
  * later processes.  The requests' outputs are written (several times).
  * Errors: as prand_batch_run. */
 prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream,
-                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, float *best_ms);
+                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, uint32_t *block,
+                                    uint32_t *row_bytes, float *best_ms);
+
+/* Sets the batched launch parameters the tuner chooses (same meanings and
+ * allowed values: section lengths multiples of 4, block 64 or 128, row_bytes
+ * 128 or 256) for later batches and plans on the current device, e.g. from a
+ * configuration kept elsewhere.  Errors: PRAND_ERR_ARG, PRAND_ERR_CUDA. */
+prand_status_t prand_batch_set_params(uint32_t seclen_mrg_lfsr, uint32_t seclen_gm, uint32_t block,
+                                      uint32_t row_bytes);
 
 /* ---- Request server (no counterpart in the paper: continuous batching of
  * stream requests, with stream states resident on the device) ----

@@ -40,7 +40,8 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_server_destroy", "prand_server_replay", "prand_convert", "prand_generate_host_u32",
            "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
            "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2", "prand_init_streams_spaced",
-           "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf", "prand_host_generate"]
+           "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf", "prand_host_generate",
+           "prand_batch_set_params"]
 
 
 class PrandError(RuntimeError):
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
     L.prand_kernel_launches.restype = u64
     L.prand_batch_run.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p]
     L.prand_mrg32k3a_generate_u32_noalloc.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p, u64, ctypes.c_void_p]
+    L.prand_batch_set_params.argtypes = [ctypes.c_uint32] * 4
     L.prand_host_generate.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, u64, ctypes.c_void_p, u64,
                                       ctypes.c_int32]
     L.prand_convert.argtypes = [ctypes.c_void_p, u64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
@@ -135,6 +137,7 @@ def load(build_if_missing: bool = False):
     L.prand_batch_plan_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     L.prand_batch_plan_destroy.argtypes = [ctypes.c_void_p]
     L.prand_batch_autotune.argtypes = [ctypes.POINTER(Request), ctypes.c_size_t, u64, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_float)]
     for nm in EXPORTS:
@@ -298,12 +301,17 @@ def prand_batch_plan_destroy(plan: int) -> None:
 
 
 def prand_batch_autotune(requests, seed: int, stream: int = 0):
-    """Returns (seclen_mrg_lfsr, seclen_gm, best_ms) and keeps them for later batches."""
+    """Returns (seclen_mrg_lfsr, seclen_gm, block, row_bytes, best_ms) and keeps
+    them for later batches."""
     arr, n = requests_array(requests)
-    a, b, t = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
+    a, b, c, d, t = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_float()
     _check(load().prand_batch_autotune(arr, n, ctypes.c_uint64(seed), stream, ctypes.byref(a), ctypes.byref(b),
-                                       ctypes.byref(t)), "prand_batch_autotune")
-    return a.value, b.value, t.value
+                                       ctypes.byref(c), ctypes.byref(d), ctypes.byref(t)), "prand_batch_autotune")
+    return a.value, b.value, c.value, d.value, t.value
+
+
+def prand_batch_set_params(seclen_mrg_lfsr: int, seclen_gm: int, block: int = 64, row_bytes: int = 128) -> None:
+    _check(load().prand_batch_set_params(seclen_mrg_lfsr, seclen_gm, block, row_bytes), "prand_batch_set_params")
 
 
 def prand_mrg32k3a_generate_u32_noalloc(dev_state: int, n_streams: int, dev_out: int, n_per_stream: int,

@@ -22,214 +22,11 @@
 #include <mutex>
 #include <vector>
 
-#include "batch.cuh"
-#include "gm_impl.cuh"
-#include "mrg_lfsr_dev.cuh"
-#include "mt_dev.cuh"
+#include "batch_kernel.cuh"
 
 namespace prand {
 
-constexpr int kBatchThreads = 64;  // small blocks: a warp on a long tile (an MT19937 jump chain) holds little besides itself
-constexpr int kWarpSmem = 5120;  // max of: MT 2 x 624 words, staged row tile 32 x 144 B, GM word slots
-
-// ------------------------------------------------------------------ MRG / LFSR tiles
-template <typename OutT>
-__device__ __forceinline__ void batch_mrg(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
-{
-    const uint64_t off = (uint64_t)lane * T.seclen;
-    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
-    uint32_t x[3], y[3];
-    const bool from_slot = T.flags & kTileFromSlot;
-    const uint32_t *src = from_slot ? (const uint32_t *)C.slots[PRAND_MRG32K3A] + 6 * (uint64_t)T.slot
-                                    : (const uint32_t *)C.base[PRAND_MRG32K3A];
-    for (int i = 0; i < 3; ++i) { x[i] = src[i]; y[i] = src[3 + i]; }
-    if (len) {
-        if (!from_slot)
-            for (int b = 0; b < 64; ++b)
-                if ((T.stream >> b) & 1u) mrg_apply_bit(C.mrg_tab, kMrgStreamShift + b, x, y);
-        const uint64_t s = T.start + off;
-        for (int b = 0; b < 64; ++b)
-            if ((s >> b) & 1u) mrg_apply_bit(C.mrg_tab, b, x, y);
-    }
-    uint32_t x0 = x[0], x1 = x[1], x2 = x[2], y0 = y[0], y1 = y[1], y2 = y[2];
-    OutT *o = (OutT *)T.out + off;
-    if (T.flags & kTileVec) {
-        fill_rows<OutT>([&]() { return mrg_next(x0, x1, x2, y0, y1, y2); },
-                        [](uint32_t u) { return Cvt<OutT, true>::f(u); }, o, len, wsm, lane);
-    } else {
-        for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT, true>::f(mrg_next(x0, x1, x2, y0, y1, y2));
-    }
-    if ((T.flags & kTileLast) && len && off + len == T.len) {
-        uint32_t *d = (uint32_t *)C.slots[PRAND_MRG32K3A] + 6 * (uint64_t)T.wslot;
-        d[0] = x0; d[1] = x1; d[2] = x2; d[3] = y0; d[4] = y1; d[5] = y2;
-    }
-}
-
-template <typename OutT>
-__device__ __forceinline__ void batch_lfsr(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
-{
-    const uint64_t off = (uint64_t)lane * T.seclen;
-    const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
-    uint32_t z[4];
-    const bool from_slot = T.flags & kTileFromSlot;
-    const uint32_t *src = from_slot ? (const uint32_t *)C.slots[PRAND_LFSR113] + 4 * (uint64_t)T.slot
-                                    : (const uint32_t *)C.base[PRAND_LFSR113];
-    for (int c = 0; c < 4; ++c) z[c] = src[c];
-    if (len) {
-        // exponent (slot ? 0 : stream * 2^34) + start + off, as 128 bits
-        const uint64_t s = T.start + off;
-        uint64_t lo = s, hi = 0;
-        if (!from_slot) {
-            const uint64_t klo = T.stream << kLfsrStreamShift, khi = T.stream >> (64 - kLfsrStreamShift);
-            lo = klo + s;
-            hi = khi + (lo < klo ? 1u : 0u);
-        }
-        for (int b = 0; b < 64; ++b)
-            if ((lo >> b) & 1u) lfsr_apply_bit(C.lfsr_tab, b, z);
-        for (int b = 0; b < 64; ++b)
-            if ((hi >> b) & 1u) lfsr_apply_bit(C.lfsr_tab, 64 + b, z);
-    }
-    uint32_t z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3];
-    OutT *o = (OutT *)T.out + off;
-    if (T.flags & kTileVec) {
-        fill_rows<OutT>([&]() { return lfsr_next(z0, z1, z2, z3); }, [](uint32_t u) { return Cvt<OutT>::f(u); }, o, len,
-                        wsm, lane);
-    } else {
-        for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(lfsr_next(z0, z1, z2, z3));
-    }
-    if ((T.flags & kTileLast) && len && off + len == T.len) {
-        uint32_t *d = (uint32_t *)C.slots[PRAND_LFSR113] + 4 * (uint64_t)T.wslot;
-        d[0] = z0; d[1] = z1; d[2] = z2; d[3] = z3;
-    }
-}
-
-// ------------------------------------------------------------------ GM / GQ tiles
-// Lane-per-point ensembles (v = 1): the warp runs one section of the tile.
-// Thread-per-stream ensembles (v = 3, 4): lane i runs section i of the tile,
-// like the MRG32K3A and LFSR113 tiles.
-template <int GEN, typename OutT>
-__device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
-{
-    using P = GmT<GEN>;
-    const uint64_t *tab = C.gm_tab[GEN - PRAND_GM19];
-    const bool from_slot = T.flags & kTileFromSlot;
-    const uint64_t *src = from_slot ? (const uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.slot
-                                    : (const uint64_t *)C.base[GEN];
-    // exponent (slot ? 0 : stream * L) + start + off, as 128 bits
-    auto exponent = [&](uint64_t off, uint64_t &lo, uint64_t &hi) {
-        const uint64_t s = T.start + off;
-        lo = s;
-        hi = 0;
-        if (!from_slot) {
-            const uint64_t klo = T.stream * P::L_, khi = __umul64hi(T.stream, P::L_);
-            lo = klo + s;
-            hi = khi + (lo < klo ? 1u : 0u);
-        }
-    };
-    if constexpr (P::lanes == 32) {
-        const uint64_t len = min((uint64_t)T.seclen, T.len);
-        if (len == 0) return;  // whole warp
-        uint64_t zp = src[lane] >> P::t, zc = src[P::s + lane] >> P::t;
-        uint64_t lo, hi;
-        exponent(0, lo, hi);
-        gm_jump128<GEN>(tab, lo, hi, zc, zp);
-        OutT *o = (OutT *)T.out;
-        uint32_t *myslot = reinterpret_cast<uint32_t *>(wsm) + 4 * lane;
-        if (T.flags & kTileVec) gm_generate_section<GEN, OutT, true>(zc, zp, lane, o, len, myslot);
-        else gm_generate_section<GEN, OutT, false>(zc, zp, lane, o, len, myslot);
-        if ((T.flags & kTileLast) && len == T.len) {
-            uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
-            d[lane] = zp << P::t;
-            d[P::s + lane] = zc << P::t;
-        }
-    } else {
-        using Z = GmZ<GEN>;
-        const uint64_t off = (uint64_t)lane * T.seclen;
-        const uint64_t len = off < T.len ? min((uint64_t)T.seclen, T.len - off) : 0;
-        Z zc[P::s], zp[P::s];
-        if (len) {
-            uint64_t lo, hi;
-            exponent(off, lo, hi);
-            gmt_load<GEN>(tab, src, src + P::s, lo, hi, zc, zp);
-        } else {
-#pragma unroll
-            for (int i = 0; i < P::s; ++i) { zc[i] = 0; zp[i] = 0; }
-        }
-        OutT *o = (OutT *)T.out + off;
-        if (T.flags & kTileVec) {
-            fill_rows<OutT, 128, true>([&]() { return gmt_next_word<GEN>(zc, zp); },
-                                       [](uint32_t u) { return Cvt<OutT>::f(u); }, o, len, wsm, lane);
-        } else {
-            for (uint64_t i = 0; i < len; ++i) o[i] = Cvt<OutT>::f(gmt_next_word<GEN>(zc, zp));
-        }
-        if ((T.flags & kTileLast) && len && off + len == T.len) {
-            uint64_t *d = (uint64_t *)C.slots[GEN] + 2 * P::s * (uint64_t)T.wslot;
-            gmt_store<GEN>(zc, zp, d, d + P::s);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ MT19937 tiles
-// Slot layout: 624 words of the current block, then the index inside it.
-template <typename OutT>
-__device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
-{
-    uint32_t *b0 = reinterpret_cast<uint32_t *>(wsm), *b1 = b0 + kMtN;
-    uint32_t idx = kMtN;
-    if (T.flags & kTileFromSlot) {
-        const uint32_t *src = (const uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.slot;
-        mt_copy_state_warp(src, b0, lane);
-        idx = src[kMtN];
-        __syncwarp();
-    } else {
-        // stream k = base advanced by k 2^432: one polynomial per nonzero hex digit of k
-        const uint32_t *src = (const uint32_t *)C.base[PRAND_MT19937];
-        bool first = true;
-        for (int i = 0; i < kMtWinPositions; ++i) {
-            const uint32_t d = (uint32_t)(T.stream >> (4 * i)) & 15u;
-            if (!d) continue;
-            mt_apply_poly_warp(C.mt_win + ((size_t)i * 16 + d) * kMtPolyWords, first ? src : b0, b0, b0, lane);
-            first = false;
-            __syncwarp();
-        }
-        if (first) {
-            mt_copy_state_warp(src, b0, lane);
-            __syncwarp();
-        }
-    }
-    OutT *o = (OutT *)T.out;
-    const uint64_t nper = T.len;
-    uint64_t done = 0;
-    if (idx < (uint32_t)kMtN) {
-        const uint32_t cnt = (uint32_t)min((uint64_t)(kMtN - idx), nper);
-        for (uint32_t t = lane; t < cnt; t += 32) o[t] = Cvt<OutT>::f(mt_temper(b0[idx + t]));
-        done = cnt;
-        idx += cnt;
-    }
-    bool in_b0 = true;
-    while (done < nper) {
-        uint64_t rem = nper - done;
-        uint32_t emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
-        mt_twist_emit<OutT>(b0, b1, lane, o + done, emit);
-        done += emit;
-        idx = emit;
-        in_b0 = false;
-        if (done >= nper) break;
-        rem = nper - done;
-        emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
-        mt_twist_emit<OutT>(b1, b0, lane, o + done, emit);
-        done += emit;
-        idx = emit;
-        in_b0 = true;
-    }
-    if (T.flags & kTileLast) {
-        const uint32_t *cur = in_b0 ? b0 : b1;
-        uint32_t *d = (uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.wslot;
-        mt_copy_state_warp(cur, d, lane);
-        if (lane == 0) d[kMtN] = idx;
-    }
-    __syncwarp();
-}
+constexpr int kBatchThreads = 64;  // the wide build: small blocks (a warp on a long tile holds little besides itself)
 
 // One MT19937 stream for the per-request form: stream k = base advanced by
 // k 2^432, one window polynomial per nonzero hex digit of k (the same jump the
@@ -237,84 +34,19 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
 __global__ void __launch_bounds__(32) mt_window_init_kernel(const uint32_t *base, const uint32_t *win, uint64_t k,
                                                             uint32_t *dst)
 {
-    __shared__ uint32_t seq[2 * kMtN];
+    __shared__ uint32_t seq[2 * kMtN], pbuf[kMtPolyWords];
     const int lane = threadIdx.x;
     bool first = true;
     for (int i = 0; i < kMtWinPositions; ++i) {
         const uint32_t d = (uint32_t)(k >> (4 * i)) & 15u;
         if (!d) continue;
-        mt_apply_poly_warp(win + ((size_t)i * 16 + d) * kMtPolyWords, first ? base : dst, dst, seq, lane);
+        mt_apply_poly_warp(win + ((size_t)i * 16 + d) * kMtPolyWords, first ? base : dst, dst, seq, pbuf, lane);
         first = false;
         __syncwarp();
     }
     if (first) mt_copy_state_warp(base, dst, lane);
 }
 
-// ------------------------------------------------------------------ the persistent kernels
-// Three builds of the same loop: MT19937 tiles (jump chains that need many
-// registers), the thread-per-stream GM/GQ tiles (8 or 12 points per lane, up
-// to 128 registers), and every other generator (48 registers, so many more
-// resident warps).  A batch's tiles come in that order (order_tiles).
-enum { kModeMt = 0, kModeRest = 1, kModeWide = 2 };
-constexpr int kModes = 3;
-
-template <typename OutT, int MODE>
-__device__ __forceinline__ void batch_tile(const BatchTile &T, const BatchCtx &C, unsigned char *wsm, int lane)
-{
-    if constexpr (MODE == kModeMt) {
-        batch_mt<OutT>(T, C, wsm, lane);
-    } else if constexpr (MODE == kModeWide) {
-        switch (T.gen) {
-        case PRAND_GM55: batch_gm<PRAND_GM55, OutT>(T, C, wsm, lane); break;
-        case PRAND_GQ58_3: batch_gm<PRAND_GQ58_3, OutT>(T, C, wsm, lane); break;
-        case PRAND_GQ58_4: batch_gm<PRAND_GQ58_4, OutT>(T, C, wsm, lane); break;
-        default: break;  // not a tile of this build (the host partitions the list)
-        }
-    } else {
-        switch (T.gen) {
-        case PRAND_MRG32K3A: batch_mrg<OutT>(T, C, wsm, lane); break;
-        case PRAND_LFSR113: batch_lfsr<OutT>(T, C, wsm, lane); break;
-        case PRAND_GM19: batch_gm<PRAND_GM19, OutT>(T, C, wsm, lane); break;
-        case PRAND_GM29: batch_gm<PRAND_GM29, OutT>(T, C, wsm, lane); break;
-        case PRAND_GM31: batch_gm<PRAND_GM31, OutT>(T, C, wsm, lane); break;
-        case PRAND_GM61: batch_gm<PRAND_GM61, OutT>(T, C, wsm, lane); break;
-        case PRAND_GQ58_1: batch_gm<PRAND_GQ58_1, OutT>(T, C, wsm, lane); break;
-        default: break;  // not a tile of this build (the host partitions the list)
-        }
-    }
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads, (MODE == kModeRest ? 20 : MODE == kModeWide ? 8 : 1)) batch_kernel(const BatchTile *__restrict__ tiles, uint32_t ntiles,
-                                                              uint32_t *counter, BatchCtx ctx)
-{
-    __shared__ __align__(16) unsigned char smem[kBatchThreads / 32][kWarpSmem];
-    const int lane = threadIdx.x & 31;
-    unsigned char *wsm = smem[threadIdx.x >> 5];
-    for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1u);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= ntiles) return;
-        const BatchTile T = tiles[t];
-        if (T.dtype == PRAND_DTYPE_U32) batch_tile<uint32_t, MODE>(T, ctx, wsm, lane);
-        else if (T.dtype == PRAND_DTYPE_F32) batch_tile<float, MODE>(T, ctx, wsm, lane);
-        else batch_tile<double, MODE>(T, ctx, wsm, lane);
-        __syncwarp();
-        if (ctx.tiles_left && lane == 0) {
-            // the request's last tile to finish publishes its completion: every
-            // tile fences its writes before counting down; the last one fences
-            // to system scope and appends the request to the host-visible list
-            __threadfence();
-            if (atomicSub(&ctx.tiles_left[T.req], 1u) == 1u) {
-                __threadfence_system();
-                const uint32_t slot = atomicAdd(ctx.done_count, 1u);
-                ctx.done_list[slot] = T.req + 1u;
-            }
-        }
-        __syncwarp();
-    }
-}
 
 // ------------------------------------------------------------------ host: engine
 namespace {
@@ -338,7 +70,9 @@ struct Engine {
     cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
     uint32_t *d_counter = nullptr;
     BatchParams params;
-    int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // per kernel build (set at engine start)
+    int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // MT19937 (one warp per tile) and wide builds
+    int mt_team_bps = 1;                               // MT19937 build with a team of warps per tile
+    int rest_bps[kRestVariants] = { 1, 1, 1, 1 };      // the rest build's variants
     cudaStream_t aux = nullptr;                   // second branch of mixed launches
     cudaEvent_t fork = nullptr, join = nullptr;
     std::mutex aux_mu;
@@ -361,14 +95,19 @@ prand_status_t engine_get(Engine **out)
         if (!dev_alloc(&E.d_counter, 64)) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
         E.sms = device_sm_count();
-        for (int m = 0; m < kModes; ++m) {
+        for (int m : { (int)kModeMt, (int)kModeWide }) {
             int bps = 0;
             const cudaError_t e = m == kModeMt
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeMt>, kBatchThreads, 0)
-                : m == kModeWide
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeWide>, kBatchThreads, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeRest>, kBatchThreads, 0);
+                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeMt, 32, 128>, 32, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeWide, kBatchThreads, 128>, kBatchThreads, 0);
             E.blocks_per_sm[m] = (e == cudaSuccess && bps >= 1) ? bps : 1;
+        }
+        for (int v = 0; v < kRestVariants; ++v) E.rest_bps[v] = rest_blocks_per_sm(v);
+        {
+            int bps = 0;
+            const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bps, batch_kernel<kModeMt, 32 * kMtTeam, 128>, 32 * kMtTeam, 0);
+            E.mt_team_bps = (e == cudaSuccess && bps >= 1) ? bps : 1;
         }
         if (cudaStreamCreateWithFlags(&E.aux, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&E.fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -378,11 +117,14 @@ prand_status_t engine_get(Engine **out)
         if (path) {
             FILE *f = fopen(path, "r");
             if (f) {
-                unsigned a = 0, b = 0;
-                if (fscanf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u", &a, &b) == 2 && a && b &&
-                    a % 4 == 0 && b % 4 == 0) {
+                unsigned a = 0, b = 0, c = 0, d = 0;
+                if (fscanf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u, \"block\": %u, \"row_bytes\": %u", &a, &b,
+                           &c, &d) == 4 && a && b && a % 4 == 0 && b % 4 == 0 && (c == 64 || c == 128) &&
+                    (d == 128 || d == 256)) {
                     E.params.seclen_mrg_lfsr = a;
                     E.params.seclen_gm = b;
+                    E.params.block = c;
+                    E.params.row_bytes = d;
                 }
                 fclose(f);
             }
@@ -549,12 +291,14 @@ prand_status_t validate_requests(const prand_request_t *reqs, size_t n)
     return PRAND_OK;
 }
 
-static unsigned batch_grid(uint32_t ntiles, int mode)
+// Persistent grid of a build: enough blocks for the tiles, at most the
+// resident blocks of the whole GPU.
+static unsigned batch_grid(uint32_t ntiles, uint32_t block, int blocks_per_sm)
 {
     Engine *E;
     if (engine_get(&E) != PRAND_OK) return 1;
-    uint64_t warps_needed = ntiles, per_block = kBatchThreads / 32;
-    uint64_t g = std::min<uint64_t>((warps_needed + per_block - 1) / per_block, (uint64_t)E->sms * E->blocks_per_sm[mode]);
+    uint64_t warps_needed = ntiles, per_block = block / 32;
+    uint64_t g = std::min<uint64_t>((warps_needed + per_block - 1) / per_block, (uint64_t)E->sms * blocks_per_sm);
     return (unsigned)std::max<uint64_t>(g, 1);
 }
 
@@ -577,7 +321,7 @@ uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt)
 // the MT19937 part runs on `aux`, forked from and joined back into `st`.
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
                             uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux,
-                            cudaEvent_t fork, cudaEvent_t join)
+                            cudaEvent_t fork, cudaEvent_t join, int mt_team)
 {
     if (cudaMemsetAsync(d_counter, 0, 3 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
     if (!ntiles) return PRAND_OK;
@@ -588,19 +332,29 @@ prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t 
         if (!aux || cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
             return PRAND_ERR_CUDA;
     }
+    Engine *E;
+    if ((s = engine_get(&E)) != PRAND_OK) return s;
     if (nmt) {
-        batch_kernel<kModeMt><<<batch_grid(nmt, kModeMt), kBatchThreads, 0, forked ? aux : st>>>(d_tiles, nmt,
-                                                                                               d_counter, ctx);
+        cudaStream_t ms = forked ? aux : st;
+        if (mt_team == kMtTeam) {
+            const unsigned g = batch_grid(nmt, 32, E->mt_team_bps);  // one tile per block
+            batch_kernel<kModeMt, 32 * kMtTeam, 128><<<g, 32 * kMtTeam, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
+        } else {
+            const unsigned g = batch_grid(nmt, 32, E->blocks_per_sm[kModeMt]);
+            batch_kernel<kModeMt, 32, 128><<<g, 32, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
+        }
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (nwide) {
-        batch_kernel<kModeWide><<<batch_grid(nwide, kModeWide), kBatchThreads, 0, st>>>(d_tiles + nmt, nwide,
-                                                                                       d_counter + 2, ctx);
+        const unsigned g = batch_grid(nwide, kBatchThreads, E->blocks_per_sm[kModeWide]);
+        batch_kernel<kModeWide, kBatchThreads, 128><<<g, kBatchThreads, 0, st>>>(d_tiles + nmt, nwide, d_counter + 2,
+                                                                               ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (nrest) {
-        batch_kernel<kModeRest><<<batch_grid(nrest, kModeRest), kBatchThreads, 0, st>>>(d_tiles + nmt + nwide, nrest,
-                                                                                        d_counter + 1, ctx);
+        const int v = rest_variant(E->params.block, E->params.row_bytes);
+        rest_launch(v, batch_grid(nrest, rest_block(v), E->rest_bps[v]), st, d_tiles + nmt + nwide, nrest,
+                    d_counter + 1, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (forked && (cudaEventRecord(join, aux) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess))
@@ -764,36 +518,57 @@ prand_status_t prand_batch_plan_destroy(prand_batch_plan_t p)
 }
 
 prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint64_t seed, prand_stream_t stream,
-                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, float *best_ms)
+                                    uint32_t *seclen_mrg_lfsr, uint32_t *seclen_gm, uint32_t *block,
+                                    uint32_t *row_bytes, float *best_ms)
 {
     prand_status_t s = validate_requests(reqs, n);
     if (s != PRAND_OK) return s;
     Engine *E;
     if ((s = engine_get(&E)) != PRAND_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t cand[] = { 2048, 8192, 32768 };
     const BatchParams keep = E->params;
     BatchParams best = keep;
     float best_t = 1e30f;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // one candidate: a graph plan with these parameters, one warm-up launch,
+    // the mean of three timed launches
+    auto try_params = [&](const BatchParams &c) {
+        E->params = c;
+        prand_batch_plan_t plan;
+        if ((s = prand_batch_plan_create(&plan, reqs, n, seed)) != PRAND_OK) return;
+        prand_batch_plan_launch(plan, stream);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) prand_batch_plan_launch(plan, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3;
+        prand_batch_plan_destroy(plan);
+        if (ms < best_t) { best_t = ms; best = c; }
+    };
+    // coordinate search: the two section lengths (outputs per lane and per
+    // warp section), then the rest build's threads per block and staged row
+    // size (outputs per row store) at the best lengths
+    const uint32_t cand[] = { 2048, 8192, 32768 };
     for (uint32_t a : cand)
         for (uint32_t b : cand) {
-            E->params.seclen_mrg_lfsr = a;
-            E->params.seclen_gm = b;
-            prand_batch_plan_t plan;
-            if ((s = prand_batch_plan_create(&plan, reqs, n, seed)) != PRAND_OK) break;
-            prand_batch_plan_launch(plan, stream);  // warm-up
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 3; ++r) prand_batch_plan_launch(plan, stream);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= 3;
-            prand_batch_plan_destroy(plan);
-            if (ms < best_t) { best_t = ms; best = E->params; }
+            if (s != PRAND_OK) break;
+            BatchParams c = keep;
+            c.seclen_mrg_lfsr = a;
+            c.seclen_gm = b;
+            try_params(c);
+        }
+    const BatchParams lengths = best;
+    for (uint32_t bs : { 64u, 128u })
+        for (uint32_t rb : { 128u, 256u }) {
+            if (s != PRAND_OK) break;
+            BatchParams c = lengths;
+            c.block = bs;
+            c.row_bytes = rb;
+            if (bs != lengths.block || rb != lengths.row_bytes) try_params(c);
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -801,16 +576,33 @@ prand_status_t prand_batch_autotune(const prand_request_t *reqs, size_t n, uint6
     if (s != PRAND_OK) return s;
     if (seclen_mrg_lfsr) *seclen_mrg_lfsr = best.seclen_mrg_lfsr;
     if (seclen_gm) *seclen_gm = best.seclen_gm;
+    if (block) *block = best.block;
+    if (row_bytes) *row_bytes = best.row_bytes;
     if (best_ms) *best_ms = best_t;
     const char *path = getenv("PRAND_TUNE_CACHE");
     if (path) {
         FILE *f = fopen(path, "w");
         if (f) {
-            fprintf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u, \"ms\": %.4f}\n", best.seclen_mrg_lfsr,
-                    best.seclen_gm, best_t);
+            fprintf(f, "{\"seclen_mrg_lfsr\": %u, \"seclen_gm\": %u, \"block\": %u, \"row_bytes\": %u, \"ms\": %.4f}\n",
+                    best.seclen_mrg_lfsr, best.seclen_gm, best.block, best.row_bytes, best_t);
             fclose(f);
         }
     }
+    return PRAND_OK;
+}
+
+prand_status_t prand_batch_set_params(uint32_t seclen_mrg_lfsr, uint32_t seclen_gm, uint32_t block, uint32_t row_bytes)
+{
+    if (seclen_mrg_lfsr == 0 || seclen_gm == 0 || seclen_mrg_lfsr % 4 || seclen_gm % 4 || (block != 64 && block != 128) ||
+        (row_bytes != 128 && row_bytes != 256))
+        return PRAND_ERR_ARG;
+    Engine *E;
+    prand_status_t s = engine_get(&E);
+    if (s != PRAND_OK) return s;
+    E->params.seclen_mrg_lfsr = seclen_mrg_lfsr;
+    E->params.seclen_gm = seclen_gm;
+    E->params.block = block;
+    E->params.row_bytes = row_bytes;
     return PRAND_OK;
 }
 

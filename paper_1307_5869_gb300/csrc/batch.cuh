@@ -40,8 +40,10 @@ struct BatchCtx {
 };
 
 struct BatchParams {
-    uint32_t seclen_mrg_lfsr = 8192;  // outputs per section, chosen by the tuner
-    uint32_t seclen_gm = 8192;
+    uint32_t seclen_mrg_lfsr = 8192;  // outputs per lane section (thread-per-section tiles), chosen by the tuner
+    uint32_t seclen_gm = 8192;        // outputs per warp section (lane-per-point GM/GQ tiles)
+    uint32_t block = 64;              // threads per block of the rest-of-generators build (64 or 128)
+    uint32_t row_bytes = 128;         // its staged row size (128 or 256 bytes: 32 or 64 u32 outputs per row store)
 };
 
 prand_status_t batch_ctx(uint64_t seed, cudaStream_t st, BatchCtx *ctx, DevTables **T);
@@ -65,8 +67,13 @@ prand_status_t validate_requests(const prand_request_t *reqs, size_t n);
 bool wide_tile_gen(int gen);
 uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles);
 uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt);
+// Warps per MT19937 tile in the build used where a request's latency matters
+// (the server); batches use one warp per tile for throughput.
+constexpr int kMtTeam = 4;
+
+// mt_team: warps per MT19937 tile (1 for throughput, kMtTeam for latency).
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
                             uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux = nullptr,
-                            cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                            cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr, int mt_team = 1);
 
 }  // namespace prand

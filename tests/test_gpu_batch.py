@@ -103,13 +103,32 @@ def test_autotune_keeps_outputs_exact():
     import torch
     spec = _spec(8, 22, 1 << 16, dts=("u32",))
     bufs, reqs = _mk(spec)
-    a, b, ms = P.prand_batch_autotune(reqs, 31)
-    assert a in (2048, 8192, 32768) and b in (2048, 8192, 32768) and ms > 0
+    a, b, bs, rb, ms = P.prand_batch_autotune(reqs, 31)
+    assert a in (2048, 8192, 32768) and b in (2048, 8192, 32768) and bs in (64, 128) and rb in (128, 256) and ms > 0
     for x in bufs:
         x.zero_()
     P.prand_batch_run(reqs, 31)
     torch.cuda.synchronize()
     _check(bufs, spec, 31, "after autotune")
+
+
+@pytest.mark.parametrize("block,row_bytes", [(64, 128), (64, 256), (128, 128), (128, 256)])
+def test_every_rest_build_exact(block, row_bytes):
+    # each build of the rest-of-generators kernel the tuner can pick (threads
+    # per block, staged row size), with short sections so requests span many
+    # tiles, on mixed generators and dtypes
+    import torch
+    spec = _spec(11, 23, 40_000)
+    bufs, reqs = _mk(spec)
+    P.prand_batch_set_params(2048, 2048, block, row_bytes)
+    try:
+        P.prand_batch_run(reqs, 77)
+        torch.cuda.synchronize()
+        _check(bufs, spec, 77, f"block {block}, rows {row_bytes}")
+    finally:
+        P.prand_batch_set_params(8192, 8192, 64, 128)
+    with pytest.raises(P.PrandError):
+        P.prand_batch_set_params(2048, 2048, 96, 128)
 
 
 def test_batched_workload_sampled():
