@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_gen_kernel(uint32_t 
 __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_level_kernel(const uint32_t *poly, uint32_t *state,
                                                                          uint64_t off, uint64_t count)
 {
-    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN];
+    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN], pbuf[kMtWarpsPerBlock][kMtPolyWords];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
     if (j >= count) return;
-    mt_apply_poly_warp(poly, state + j * kMtN, state + (off + j) * kMtN, seq[w], lane);
+    mt_apply_poly_warp(poly, state + j * kMtN, state + (off + j) * kMtN, seq[w], pbuf[w], lane);
 }
 
 // Every stream advanced by the set bits of a 512-bit offset (one polynomial
@@ -113,7 +113,7 @@ struct MtBits { uint64_t w[8]; };
 __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_multi_kernel(const uint32_t *polys, uint32_t *state,
                                                                          uint64_t n, MtBits e, uint32_t *scratch)
 {
-    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN];
+    __shared__ uint32_t seq[kMtWarpsPerBlock][2 * kMtN], pbuf[kMtWarpsPerBlock][kMtPolyWords];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t j = (uint64_t)blockIdx.x * kMtWarpsPerBlock + w;
     if (j >= n) return;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(32 * kMtWarpsPerBlock) mt_multi_kernel(const u
     for (int b = 0; b < 512; ++b) {
         if (!((e.w[b >> 6] >> (b & 63)) & 1u)) continue;
         // result goes to registers then back over s (src is copied to smem first)
-        mt_apply_poly_warp(polys + (size_t)b * kMtPolyWords, s, s, seq[w], lane);
+        mt_apply_poly_warp(polys + (size_t)b * kMtPolyWords, s, s, seq[w], pbuf[w], lane);
         __syncwarp();
     }
     (void)scratch;

@@ -96,48 +96,66 @@ __device__ __forceinline__ void mt_twist_block(const uint32_t *ob, uint32_t *nb,
     }
 }
 
-// dst := g(A) src for one stream, by one warp (eq. (g_v)).  With src in window
-// form x_0..x_623, A^i src is the window x_i..x_{i+623}, so result word m is the
-// XOR of x_{i+m} over the set coefficients i of g.  Lane l owns 20 consecutive
-// result words m = mbase + j (mbase = 20 l, and 604 for lane 31, whose first 16
-// words repeat lane 30's) and keeps the 20 sequence words x_{i+mbase..i+mbase+19}
-// in registers as a window that slides by one word per coefficient: one
-// shared-memory load per coefficient, and 20 register XORs per set coefficient
-// (one three-input XOR when two neighbouring coefficients are both set).
-// seq is a 1248-word ring holding two consecutive 624-word blocks (x at index
-// i sits at seq[i mod 1248]); the block two ahead is twisted into the oldest
-// slot once no lane will load from it again (loads at step i reach x_{i+19}
-// .. x_{i+623}).  src may equal dst or seq.
-__device__ inline void mt_apply_poly_warp(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst,
-                                          uint32_t *seq, int lane)
+// dst := the part of g(A) src that coefficients [c0, c1) of g contribute to
+// result words [m0, m1), for one stream, by one warp (eq. (g_v)).  poly: g's
+// 624 coefficient words, staged in shared memory by the caller.
+//
+// With src in window form x_0..x_623, A^i src is the window x_i..x_{i+623}, so
+// result word m is the XOR of x_{i+m} over the set coefficients i of g.  Lane
+// l owns W consecutive result words m = mbase + j (mbase = m0 + W l, clamped to
+// m1 - W; a clamped lane writes only the words past the previous lane's) and
+// keeps the W sequence words x_{i+mbase..i+mbase+W-1} in registers as a window
+// that slides by one word per coefficient: one shared-memory load per
+// coefficient, and W register XORs per set coefficient (one three-input XOR
+// when two neighbouring coefficients are both set; W is even).  seq is this
+// warp's 1248-word ring holding two consecutive 624-word blocks of the
+// sequence (x at index i sits at seq[i mod 1248]): blocks 0 and 1 are made
+// from src, and the warp twists on to the blocks around c0 before its first
+// coefficient; block b then replaces block b - 2 at the first chunk of W
+// coefficients from which no lane loads below index 624 (b - 1) again (loads
+// from chunk start i0 on reach x_{i0+m0+W-1} and up).  c0 and c1 are multiples
+// of W.  src and dst may be the same buffer only when every warp that reads
+// src has copied it before any warp writes dst (sync: called between the two).
+template <int W, typename Sync>
+__device__ inline void mt_apply_poly_part(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst,
+                                          uint32_t *seq, int lane, int m0, int m1, int c0, int c1, Sync &&sync)
 {
-    constexpr int W = 20, RING = 2 * kMtN;
-    const int mbase = lane < 31 ? W * lane : kMtN - W;
+    static_assert(W % 2 == 0 && W <= 32, "pairs of coefficients per step");
+    constexpr int RING = 2 * kMtN;
+    const int mwant = m0 + W * lane;
+    const int mbase = mwant + W <= m1 ? mwant : m1 - W;
     uint32_t acc[W], win[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
     mt_copy_state_warp(src, seq, lane);
     __syncwarp();
+    sync();  // every warp holds its copy of src
     mt_twist_block(seq, seq + kMtN, lane);  // block 1 into slot 1
+    const int b0 = c0 / kMtN;
+    for (int b = 2; b <= b0 + 1; ++b) {  // blocks b0 and b0 + 1 in the ring
+        __syncwarp();
+        mt_twist_block(seq + ((b - 1) & 1) * kMtN, seq + (b & 1) * kMtN, lane);
+    }
+    __syncwarp();
 #pragma unroll
-    for (int j = 0; j < W - 1; ++j) win[j] = seq[mbase + j];
-    int next_block = 2;
-    int p0 = mbase + W - 1;  // ring position of the word loaded at step i0
-    for (int i0 = 0; i0 < kMtDeg; i0 += W) {
-        if (next_block <= 32 && i0 >= kMtN * (next_block - 2) + 605) {
+    for (int j = 0; j < W - 1; ++j) win[j] = seq[(c0 + mbase + j) % RING];
+    int next_block = b0 + 2;
+    int p0 = (c0 + mbase + W - 1) % RING;  // ring position of the word loaded at step i0
+    for (int i0 = c0; i0 < c1; i0 += W) {
+        if (next_block <= 32 && i0 >= kMtN * (next_block - 1) - m0 - W + 1) {
             __syncwarp();
             mt_twist_block(seq + ((next_block - 1) & 1) * kMtN, seq + (next_block & 1) * kMtN, lane);
             ++next_block;
         }
         const int w = i0 >> 5, sh = i0 & 31;
-        const uint64_t two = (uint64_t)__ldg(poly + w) | ((uint64_t)(w + 1 < kMtPolyWords ? __ldg(poly + w + 1) : 0u) << 32);
-        const uint32_t bits = (uint32_t)(two >> sh) & ((1u << W) - 1u);
+        const uint64_t two = (uint64_t)poly[w] | ((uint64_t)(w + 1 < kMtPolyWords ? poly[w + 1] : 0u) << 32);
+        const uint32_t bits = (uint32_t)(two >> sh) & (uint32_t)((1ull << W) - 1u);
 #pragma unroll
         for (int u = 0; u < W; u += 2) {
             // step u: window slots (u + j) % W hold x_{i0+u+mbase+j}; the newest,
-            // x_{i0+u+mbase+19}, goes into slot (u + 19) % W.  Step u + 1 needs
-            // x_{i0+u+1+mbase+19} as its j = 19 word (nx); it replaces the oldest
-            // word (slot u % W) only after both steps are applied.
+            // x_{i0+u+mbase+W-1}, goes into slot (u + W - 1) % W.  Step u + 1 needs
+            // x_{i0+u+1+mbase+W-1} as its j = W - 1 word (nx); it replaces the
+            // oldest word (slot u % W) only after both steps are applied.
             int pa = p0 + u, pb = p0 + u + 1;
             if (pa >= RING) pa -= RING;
             if (pb >= RING) pb -= RING;
@@ -160,10 +178,51 @@ __device__ inline void mt_apply_poly_warp(const uint32_t *__restrict__ poly, con
         if (p0 >= RING) p0 -= RING;
     }
     __syncwarp();
+    const int jfirst = mwant - mbase;  // words of this lane not already written by the previous lane
 #pragma unroll
     for (int j = 0; j < W; ++j)
-        if (lane < 31 || j >= W - 4) dst[mbase + j] = acc[j];
+        if (j >= jfirst) dst[mbase + j] = acc[j];
     __syncwarp();
+}
+
+constexpr int kMtChunkW = 20;                                       // result words per lane, coefficients per chunk
+constexpr int kMtChunks = (kMtDeg + kMtChunkW - 1) / kMtChunkW;     // 997 chunks of coefficients
+
+// dst := g(A) src for one stream by one warp (lane l owns 20 result words);
+// poly in global memory, staged into pbuf (624 shared words of this warp).
+__device__ inline void mt_apply_poly_warp(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst,
+                                          uint32_t *seq, uint32_t *pbuf, int lane)
+{
+    mt_copy_state_warp(poly, pbuf, lane);  // 624 words, as a state
+    __syncwarp();
+    mt_apply_poly_part<kMtChunkW>(pbuf, src, dst, seq, lane, 0, kMtN, 0, kMtChunkW * kMtChunks, [] {});
+}
+
+// The same by a team of T warps of one block (T = blockDim.x / 32), for one
+// stream's latency: the coefficients are split in T consecutive ranges, warp w
+// computes its range's contribution to all 624 result words into part[w]
+// (T x 624 shared words), each warp making its own copy of the sequence up to
+// its range, and the result is the XOR of the T parts (the sum of eq. (g_v) is
+// linear over GF(2)).  The team stages the polynomial into pbuf (624 shared
+// words) first; the block barrier after the copies of src lets dst alias src.
+template <int T>
+__device__ inline void mt_apply_poly_team(const uint32_t *__restrict__ poly, const uint32_t *src, uint32_t *dst,
+                                          uint32_t *seq, uint32_t *pbuf, uint32_t *part, int warp, int lane)
+{
+    const int c0 = kMtChunkW * (kMtChunks * warp / T), c1 = kMtChunkW * (kMtChunks * (warp + 1) / T);
+    for (int i = threadIdx.x; i < kMtPolyWords; i += 32 * T) pbuf[i] = poly[i];
+    mt_apply_poly_part<kMtChunkW>(pbuf, src, T == 1 ? dst : part + warp * kMtN, seq, lane, 0, kMtN, c0, c1,
+                                  [] { __syncthreads(); });
+    __syncthreads();
+    if constexpr (T > 1) {
+        for (int m = threadIdx.x; m < kMtN; m += 32 * T) {
+            uint32_t r = 0;
+#pragma unroll
+            for (int w = 0; w < T; ++w) r ^= part[w * kMtN + m];
+            dst[m] = r;
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace prand
