@@ -496,8 +496,15 @@ __device__ __forceinline__ void gm_generate_section(uint64_t &zc64, uint64_t &zp
 // the stream's next state and writes it to state_out (a separate buffer when a
 // stream is split into several sections, so no warp reads a state another
 // warp has already replaced).
+//
+// Residency: GM61, GM29 and GM31 keep their pipes busiest with eight 256-thread
+// blocks per SM (32 registers; ptxas moves a few loop-invariant words to the
+// stack); GM19 and GQ58.1 run best at six (40 registers).
+template <int GEN>
+constexpr int gm_blocks_per_sm() { return GEN == PRAND_GM61 || GEN == PRAND_GM29 || GEN == PRAND_GM31 ? 8 : 6; }
+
 template <int GEN, typename OutT, bool VEC>
-__global__ void __launch_bounds__(256) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
+__global__ void __launch_bounds__(256, gm_blocks_per_sm<GEN>()) gm_gen_kernel(const uint64_t *__restrict__ tab, const uint64_t *state_in,
                                                      uint64_t *state_out, uint64_t nstreams, uint64_t stride,
                                                      uint64_t nper, uint32_t nsec, uint64_t seclen,
                                                      OutT *__restrict__ out)
