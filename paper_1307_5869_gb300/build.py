@@ -20,7 +20,7 @@ LIB_NAME = "libprand_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "-I", os.path.join(ROOT, "include")]
 SOURCES = ["capi.cu", "gen_mrg_lfsr.cu", "gen_mt.cu", "mt_poly.cpp", "gm_dispatch.cpp", "host_simd.cpp", "batch.cu", "batch_rest_64.cu", "batch_rest_128.cu", "serve.cu", "convert.cu", "states.cu", "stats.cu"] + [
     f"gm_{g}.cu" for g in ("gm19", "gm29", "gm31", "gm55", "gm61", "gq58_1", "gq58_3", "gq58_4")]
 

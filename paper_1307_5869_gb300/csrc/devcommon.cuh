@@ -119,16 +119,13 @@ __device__ __forceinline__ uint64_t addmod_p(uint64_t a, uint64_t b)
 }
 
 // ---------------------------------------------------------------- floats
-// f32 = (u >> 8) * 2^-24: the 24-bit integer converts exactly, the scale is a
-// power of two.  u >> 8 is taken as the high word of u 2^24, a multiply, so the
-// integer ALU pipe (the bound of the cheapest generators) carries one
-// operation fewer.
-__device__ __forceinline__ float u32_to_f32(uint32_t u)
-{
-    uint32_t hi;
-    asm("mul.hi.u32 %0, %1, 16777216;" : "=r"(hi) : "r"(u));
-    return __uint2float_rn(hi) * 0x1p-24f;
-}
+// f32 = (u >> 8) * 2^-24, formed as (u & 0xFFFFFF00) * 2^-32: the masked word
+// has at most 24 significant bits, so it converts exactly (in any rounding
+// mode), and the scale is a power of two whose product stays normal (the
+// smallest nonzero value is 2^-24).  The mask folds into the logic operation
+// that forms u in the cheapest generators (LFSR113's XOR of its components),
+// so no shift is spent on either integer pipe.
+__device__ __forceinline__ float u32_to_f32(uint32_t u) { return __uint2float_rz(u & 0xFFFFFF00u) * 0x1p-32f; }
 
 // f64 = u * 2^-32, assembled from the bits (exact) to stay off the FP64 pipe.
 __device__ __forceinline__ double u32_to_f64(uint32_t u)

@@ -93,26 +93,80 @@ int berlekamp_massey(const std::vector<uint8_t> &s, Poly &C)
     return L;
 }
 
+// Reduction modulo phi eight coefficients at a time.  For every byte t, P_t is
+// the multiple of phi whose coefficients kDeg .. kDeg + 7 are the bits of t and
+// whose higher ones vanish (t x^kDeg minus the multiple is the remainder of t
+// x^kDeg).  XORing P_t x^(8 c) into r, with t the byte of r at kDeg + 8 c,
+// clears that byte; bytes are cleared from the top down.  Eight bytes are
+// cleared per pass over r: their t are found one after another from r and
+// the bytes that the P_t above them leave just below their own top (tables
+// below[1..7]), and the eight shifted P_t are then added in one pass.  Shifts
+// by whole bytes are byte offsets (bit i of a polynomial is bit i % 8 of byte
+// i / 8 in the little-endian word arrays on both host architectures).
+static_assert(__BYTE_ORDER__ == __ORDER_LITTLE_ENDIAN__, "byte offsets assume little-endian words");
+
+inline uint64_t ld64(const unsigned char *p) { uint64_t v; memcpy(&v, p, 8); return v; }
+inline void st64(unsigned char *p, uint64_t v) { memcpy(p, &v, 8); }
+
 struct Reducer {
-    // phi shifted left by 0..63 bits
-    std::vector<Poly> sh;
+    static constexpr int kPB = ((kDeg + 8 + 7) / 8 + 7) / 8 * 8;  // bytes of P_t, rounded to words
+    static constexpr int kRow = 8 + kPB + 16;                      // zero bytes before and after
+    std::vector<unsigned char> tab;                                 // [256][kRow]
+    uint8_t below[8][256];                                          // below[k][t]: P_t bits kDeg-8k .. kDeg-8k+7
     explicit Reducer(const Poly &phi)
     {
-        sh.assign(64, Poly((size_t)kW, 0));
-        for (int s = 0; s < 64; ++s)
+        const int nw = kPB / 8 + 1;
+        std::vector<Poly> phs(8, Poly((size_t)nw, 0));  // phi x^k, k = 0..7
+        for (int k = 0; k < 8; ++k)
             for (int j = 0; j <= kDeg; ++j)
-                if (getb(phi, j)) flipb(sh[(size_t)s], j + s);
+                if (getb(phi, j)) flipb(phs[(size_t)k], j + k);
+        tab.assign((size_t)256 * kRow, 0);
+        Poly T((size_t)nw, 0);
+        for (int t = 0; t < 256; ++t) {
+            std::fill(T.begin(), T.end(), 0ull);
+            for (int k = 0; k < 8; ++k)
+                if ((t >> k) & 1) flipb(T, kDeg + k);
+            for (int k = 7; k >= 0; --k)
+                if (getb(T, kDeg + k))
+                    for (int w = 0; w < nw; ++w) T[(size_t)w] ^= phs[(size_t)k][(size_t)w];
+            // T is now the remainder; P_t = T + t x^kDeg
+            for (int k = 0; k < 8; ++k)
+                if ((t >> k) & 1) flipb(T, kDeg + k);
+            memcpy(tab.data() + (size_t)t * kRow + 8, T.data(), (size_t)kPB);
+            for (int k = 0; k < 8; ++k) {
+                uint8_t b = 0;
+                for (int i = 0; i < 8; ++i) b |= (uint8_t)(getb(T, kDeg - 8 * k + i) << i);
+                below[k][t] = b;
+            }
+        }
     }
-    // r (degree < 2*kDeg) mod phi, in place
+    static uint8_t byte_at(const unsigned char *r, int pos)  // bits pos .. pos + 7
+    {
+        return (uint8_t)(((unsigned)r[pos >> 3] | ((unsigned)r[(pos >> 3) + 1] << 8)) >> (pos & 7));
+    }
+    // clears bytes c0 .. c0 + n - 1 (n <= 8) of the part above kDeg
+    void group(unsigned char *r, int c0, int n) const
+    {
+        uint8_t t[8] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+        for (int j = n - 1; j >= 0; --j) {
+            uint8_t b = byte_at(r, kDeg + 8 * (c0 + j));
+            for (int k = j + 1; k < n; ++k) b ^= below[k - j][t[k]];
+            t[j] = b;
+        }
+        const unsigned char *P[8];
+        for (int j = 0; j < 8; ++j) P[j] = tab.data() + (size_t)t[j] * kRow + 8 - j;
+        unsigned char *R = r + c0;
+        for (int i = 0; i < kPB + 8; i += 8)
+            st64(R + i, ld64(R + i) ^ ld64(P[0] + i) ^ ld64(P[1] + i) ^ ld64(P[2] + i) ^ ld64(P[3] + i) ^ ld64(P[4] + i) ^
+                            ld64(P[5] + i) ^ ld64(P[6] + i) ^ ld64(P[7] + i));
+    }
+    // r (degree <= 2 kDeg, kW words) mod phi, in place
     void reduce(Poly &r) const
     {
-        for (int i = 2 * kDeg; i >= kDeg; --i) {
-            if (!getb(r, i)) continue;
-            int s = i - kDeg, w = s >> 6;
-            const Poly &P = sh[(size_t)(s & 63)];
-            const int nw = (kDeg + 64) / 64 + 1;
-            for (int k = 0; k < nw && w + k < kW; ++k) r[(size_t)(w + k)] ^= P[(size_t)k];
-        }
+        unsigned char *rb = reinterpret_cast<unsigned char *>(r.data());
+        int c = kDeg / 8;  // top byte
+        for (; c >= 7; c -= 8) group(rb, c - 7, 8);
+        if (c >= 0) group(rb, 0, c + 1);
     }
 };
 
@@ -135,27 +189,36 @@ void square_into(const Poly &a, Poly &out)
     }
 }
 
-// a * b (degrees < kDeg, carry-less) into out, reduced mod phi.  For every set
-// bit of b, a copy of a shifted by that bit is added: the 64 shifts of a within
-// a word are made once, so each set bit costs one pass over a's words.
+// a * b (degrees < kDeg, carry-less) into out, reduced mod phi.  The products
+// of a with every byte t are tabulated (each is the previous one with the
+// lowest set bit of t removed, plus a x^k for that bit); eight bytes of b are
+// then added per pass, each as its row at the byte's offset.
 void mul_into(const Poly &a, const Poly &b, Poly &out, const Reducer &red)
 {
-    const int nw = (kDeg + 63) / 64;  // words of a reduced polynomial
-    std::vector<Poly> sh(64, Poly((size_t)nw + 1, 0));
-    for (int s = 0; s < 64; ++s)
-        for (int w = 0; w <= nw; ++w) {
-            const uint64_t lo = w < nw ? a[(size_t)w] : 0, prev = w > 0 ? a[(size_t)(w - 1)] : 0;
-            sh[(size_t)s][(size_t)w] = s ? (lo << s) | (prev >> (64 - s)) : lo;
+    constexpr int kPB = Reducer::kPB, kRow = Reducer::kRow, nw = kPB / 8;
+    std::vector<Poly> ash(8, Poly((size_t)nw, 0));  // a x^k, k = 0..7 (degree < kDeg + 7)
+    for (int k = 0; k < 8; ++k)
+        for (int w = 0; w < nw; ++w) {
+            const uint64_t lo = a[(size_t)w], prev = w > 0 ? a[(size_t)(w - 1)] : 0;
+            ash[(size_t)k][(size_t)w] = k ? (lo << k) | (prev >> (64 - k)) : lo;
         }
+    std::vector<unsigned char> rows((size_t)256 * kRow, 0);
+    for (int t = 1; t < 256; ++t) {
+        const unsigned char *src = rows.data() + (size_t)(t & (t - 1)) * kRow + 8;
+        unsigned char *dst = rows.data() + (size_t)t * kRow + 8;
+        const uint64_t *A = ash[(size_t)__builtin_ctz((unsigned)t)].data();
+        for (int w = 0; w < nw; ++w) st64(dst + 8 * w, ld64(src + 8 * w) ^ A[w]);
+    }
     std::fill(out.begin(), out.end(), 0ull);
-    for (int w = 0; w < nw; ++w) {
-        uint64_t v = b[(size_t)w];
-        while (v) {
-            const int s = __builtin_ctzll(v);
-            v &= v - 1;
-            const Poly &A = sh[(size_t)s];
-            for (int k = 0; k <= nw; ++k) out[(size_t)(w + k)] ^= A[(size_t)k];
-        }
+    const unsigned char *bb = reinterpret_cast<const unsigned char *>(b.data());
+    unsigned char *ob = reinterpret_cast<unsigned char *>(out.data());
+    for (int g = 0; g < (kDeg + 7) / 8; g += 8) {
+        const unsigned char *P[8];
+        for (int j = 0; j < 8; ++j) P[j] = rows.data() + (size_t)bb[g + j] * kRow + 8 - j;
+        unsigned char *R = ob + g;
+        for (int i = 0; i < kPB + 8; i += 8)
+            st64(R + i, ld64(R + i) ^ ld64(P[0] + i) ^ ld64(P[1] + i) ^ ld64(P[2] + i) ^ ld64(P[3] + i) ^ ld64(P[4] + i) ^
+                            ld64(P[5] + i) ^ ld64(P[6] + i) ^ ld64(P[7] + i));
     }
     red.reduce(out);
 }
