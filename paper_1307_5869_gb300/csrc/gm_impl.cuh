@@ -247,9 +247,9 @@ __device__ __forceinline__ bool gm_strip1(uint32_t z)  // v = 1, p < 2^32: canon
 
 // v = 3, 4: the strip of point I placed at bit v I of the word w.  For
 // p = 2^b - c, 2^v z = q0 2^b + r0 with q0 = z >> (b - v), and
-// floor(2^v z / p) = q0 + [r0 + c q0 >= p] = (2^v z + c q0 + c) >> b, one
-// 64-bit multiply-add; its low v bits are taken by a funnel shift that moves
-// bit b to bit v I, and a mask.  A lazy z in [p, p + slack) gives 2^v, whose
+// floor(2^v z / p) = q0 + [r0 + c q0 >= p] = (2^v z + c q0 + c) >> b (a
+// 64-bit sum for GM55, a 32-bit one for p = 2^29 - 3); its low v bits are
+// moved to bit v I by a shift and kept by a mask.  A lazy z in [p, p + slack) gives 2^v, whose
 // low v bits are 0, the strip of z - p.  Bits beyond 31 are dropped (GQ58.3's
 // point 10 keeps 2 of its 3 bits, point 11 none).
 template <int GEN, int I>
@@ -268,15 +268,22 @@ __device__ __forceinline__ uint32_t gm_strip_insert(GmZ<GEN> z, uint32_t w)
         const uint32_t x = pos <= 19 ? hi >> (19 - pos) : hi << (pos - 19);
         return (x & (15u << pos)) | w;
     } else {
-        // p = 2^29 - 3, lazy z < 2^29 + 312: X = 2^v z + 3 (q0 + 1) < 2^34
+        // p = 2^29 - 3, lazy z < 2^29 + 312: X = 2^v z + 3 (q0 + 1) < 2^34, but
+        // only bits 29 .. 29 + v - 1 are wanted, so 32 bits suffice: for v = 3
+        // they are bits 29..31 of X mod 2^32; for v = 4, bits 28..31 of
+        // X / 2 = 8 z + floor(3 (q0 + 1) / 2) mod 2^32 (2^v z is even).  The
+        // only wrap past 2^32 comes from a lazy z >= p, whose strip bits are 0
+        // either way.  No wide multiply: the FMA-heavy pipe, which the step's
+        // products keep busy, is spared.
+        static_assert(v == 3 || v == 4, "thread-per-stream strips are 3 or 4 bits");
+        constexpr int top = v == 4 ? 28 : 29;
         const uint32_t q0 = z >> (29 - v);
-        const uint64_t X = (uint64_t)z * (1u << v) + (3u * q0 + 3u);
-        const uint32_t lo = (uint32_t)X, hi = (uint32_t)(X >> 32);
-        uint32_t x;
-        if constexpr (pos <= 29) x = __funnelshift_r(lo, hi, 29 - pos);
-        else x = lo << (pos - 29);
+        const uint32_t x = v == 4 ? 8u * z + ((3u * q0 + 3u) >> 1) : 8u * z + 3u * q0 + 3u;
+        uint32_t y;
+        if constexpr (pos <= top) y = x >> (top - pos);
+        else y = x << (pos - top);
         constexpr uint32_t mask = pos + v <= 32 ? ((1u << v) - 1u) << pos : 0xFFFFFFFFu << pos;
-        return (x & mask) | w;
+        return (y & mask) | w;
     }
 }
 

@@ -125,15 +125,14 @@ def strip_insert(gen, i, z, w=0):
         hi = X >> 32
         x = hi >> (19 - pos) if pos <= 19 else (hi << (pos - 19)) & M32
         return (x & (15 << pos)) | w
+    # p = 2^29 - 3: the kernel works in 32 bits, on X mod 2^32 (v = 3) or
+    # X / 2 mod 2^32 (v = 4), X = 2^v z + 3 (q0 + 1)
     q0 = z >> (29 - v)
-    X = (z * (1 << v) + ((3 * q0 + 3) & M32)) & M64
-    lo, hi = X & M32, X >> 32
-    if pos <= 29:
-        x = ((((hi << 32) | lo) >> (29 - pos)) & M32)
-    else:
-        x = (lo << (pos - 29)) & M32
+    top = 28 if v == 4 else 29
+    x = (8 * z + ((3 * q0 + 3) >> 1 if v == 4 else 3 * q0 + 3)) & M32
+    y = x >> (top - pos) if pos <= top else (x << (pos - top)) & M32
     mask = (((1 << v) - 1) << pos) if pos + v <= 32 else (M32 << pos) & M32
-    return (x & mask) | w
+    return (y & mask) | w
 
 
 def next_lazy(gen, z, y):
