@@ -46,10 +46,10 @@ STATE_BYTES = {"MT19937": 624 * 4, "MRG32K3A": 24, "LFSR113": 16, "GM19": 32 * 1
 # multiply-add counts as two operations): GM/GQ = the points' steps (the
 # recurrence and its fold), strips and word assembly; MRG32K3A = its two
 # component steps and the combination.  Per point step: GM19, GM29 7; GM31,
-# GQ58.1 10; GM61 16; GM55 20; GQ58.3, GQ58.4 13 (GQ58.3's point 11 steps
-# without a strip: 7).
+# GQ58.1 10; GM61 16; GM55 20; GQ58.3 12, GQ58.4 13 (a 7-operation step and a
+# 32-bit strip of 5 or 6; GQ58.3's point 11 steps without a strip: 7).
 OPS_PER_WORD = {"GM19": 32 * 7, "GM29": 32 * 7, "GM31": 32 * 10, "GM55": 8 * 20, "GM61": 32 * 16,
-                "GQ58_1": 32 * 10, "GQ58_3": 11 * 13 + 7, "GQ58_4": 8 * 13, "MRG32K3A": 28}
+                "GQ58_1": 32 * 10, "GQ58_3": 11 * 12 + 7, "GQ58_4": 8 * 13, "MRG32K3A": 28}
 # int32 lanes per SM: four schedulers, each issuing one 32-lane warp instruction per
 # cycle (the issue-slot bound of an integer kernel; the SM count and clock are
 # queried at run time)
