@@ -82,6 +82,29 @@ def test_strip_insert_is_the_strip(gen):
             assert KM.strip_insert(gen, i, z, 0xFFFFFFFF) == 0xFFFFFFFF
 
 
+@pytest.mark.parametrize("gen", ["GQ58_3", "GQ58_4"])
+def test_gq58_strip_in_32_bits_over_the_whole_lazy_range(gen):
+    # The v = 3, 4 kernels take the strip from a 32-bit sum (8 z + 3 (q0 + 1),
+    # halved in its constant for v = 4) instead of the 64-bit 2^v z + 3 (q0 + 1).
+    # Every lazy residue z in [0, p + slack) is checked against
+    # floor(2^v (z mod p) / p) mod 2^v; a wrong shift, constant or wrap fails.
+    v, slack = KM.PARAMS[gen][4], KM.PARAMS[gen][6]
+    p = KM.PARAMS[gen][2]
+    top = 28 if v == 4 else 29
+    # uint32 arithmetic wraps mod 2^32 as the kernel's does; the exact strip
+    # floor(2^v zm / p) is taken in doubles, exact here (the quotient is never
+    # closer than 1/p ~ 2^-29 to an integer, far above the rounding error)
+    step = 1 << 25
+    for lo in range(0, p + slack, step):
+        z = np.arange(lo, min(lo + step, p + slack), dtype=np.uint32)
+        q0 = z >> np.uint32(29 - v)
+        c = (np.uint32(3) * q0 + np.uint32(3)) >> np.uint32(1) if v == 4 else np.uint32(3) * q0 + np.uint32(3)
+        got = ((np.uint32(8) * z + c) >> np.uint32(top)) & np.uint32((1 << v) - 1)
+        zm = np.where(z >= np.uint32(p), z - np.uint32(p), z)
+        want = np.floor(zm.astype(np.float64) * float(1 << v) / float(p)).astype(np.uint32) & np.uint32((1 << v) - 1)
+        assert np.array_equal(got, want), lo
+
+
 @pytest.mark.parametrize("gen", GENS)
 def test_lazy_state_search_reaches_the_lazy_range(gen):
     # the states the GPU edge-case tests import: the model shows that their
