@@ -186,6 +186,19 @@ uint64_t prand_device_state_bytes(prand_gen_t gen);
 prand_status_t prand_export_states(prand_handle_t h, void *dev_states, prand_stream_t stream);
 prand_status_t prand_import_states(prand_handle_t h, const void *dev_states, prand_stream_t stream);
 
+/* The MT19937 jump polynomial g(x) = x^(2^b) mod phi(x), b = 0..511 (Sec. 5.4:
+ * the stored family g_v with v = 2^b; phi is the characteristic polynomial of
+ * the one-output state transition A, degree 19937).  A state advanced by 2^b
+ * outputs is g(A) applied to it (eq. (g_v)), which a kernel of the caller's can
+ * evaluate on states from prand_export_states.  Writes 624 words to host_out
+ * (caller-owned host memory): the coefficient of x^i is bit i % 32 of word
+ * i / 32; bits 19937..19967 are zero.  Host-only and thread-safe; the first
+ * call of the process computes the family (phi by Berlekamp-Massey, then 511
+ * squarings mod phi, about 0.1 s), later calls copy.
+ * Errors: PRAND_ERR_ARG (b > 511 or host_out NULL), PRAND_ERR_STATE (the
+ * family could not be computed; not expected). */
+prand_status_t prand_mt_jump_polynomial(uint32_t b, uint32_t *host_out);
+
 /* Advance every stream of the handle by the 256-bit offset offset_le[0] +
  * 2^64 offset_le[1] + 2^128 offset_le[2] + 2^192 offset_le[3] outputs
  * (rng_skipahead_, Sec. 7.2; jump methods of Sec. 5.1-5.4).

@@ -41,7 +41,7 @@ EXPORTS = ["prand_create", "prand_init_streams", "prand_generate_u32", "prand_ge
            "prand_generate_host_f32", "prand_generate_host_f64", "prand_device_state_bytes", "prand_export_states",
            "prand_import_states", "prand_init_streams_variant", "prand_skipahead_pow2", "prand_init_streams_spaced",
            "prand_test_cells", "prand_test_counts", "prand_test_evaluate", "prand_chi2_sf", "prand_host_generate",
-           "prand_batch_set_params"]
+           "prand_batch_set_params", "prand_mt_jump_polynomial"]
 
 
 class PrandError(RuntimeError):
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = False):
     L.prand_host_generate.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_void_p, u64, ctypes.c_void_p, u64,
                                       ctypes.c_int32]
     L.prand_convert.argtypes = [ctypes.c_void_p, u64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    L.prand_mt_jump_polynomial.argtypes = [ctypes.c_uint32, ctypes.c_void_p]
     L.prand_device_state_bytes.argtypes = [ctypes.c_int]
     L.prand_device_state_bytes.restype = u64
     L.prand_export_states.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p]
@@ -199,6 +200,13 @@ def prand_generate_host_f32(h: int, host_out: int, n_per_stream: int, stream: in
 
 def prand_generate_host_f64(h: int, host_out: int, n_per_stream: int, stream: int = 0) -> None:
     _check(load().prand_generate_host_f64(h, host_out, n_per_stream, stream), "prand_generate_host_f64")
+
+
+def prand_mt_jump_polynomial(b: int) -> int:
+    """x^(2^b) mod phi for MT19937 as a Python int (bit i = coefficient of x^i)."""
+    buf = (ctypes.c_uint32 * 624)()
+    _check(load().prand_mt_jump_polynomial(b, ctypes.cast(buf, ctypes.c_void_p)), "prand_mt_jump_polynomial")
+    return sum(int(w) << (32 * i) for i, w in enumerate(buf))
 
 
 def prand_device_state_bytes(gen) -> int:

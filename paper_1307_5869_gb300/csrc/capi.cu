@@ -505,6 +505,15 @@ prand_status_t prand_generate_host_f64(prand_handle_t h, double *host_out, uint6
     return generate_host(h, host_out, PRAND_DTYPE_F64, n_per_stream, stream);
 }
 
+prand_status_t prand_mt_jump_polynomial(uint32_t b, uint32_t *host_out)
+{
+    if (b >= (uint32_t)kMtPolyCount || !host_out) return PRAND_ERR_ARG;
+    const uint32_t *polys = mt_host_pow2_polys();
+    if (!polys) return PRAND_ERR_STATE;
+    memcpy(host_out, polys + (size_t)b * kMtPolyWords, (size_t)kMtPolyWords * sizeof(uint32_t));
+    return PRAND_OK;
+}
+
 uint64_t prand_device_state_bytes(prand_gen_t gen)
 {
     return (gen < 0 || gen >= PRAND_NUM_GENERATORS) ? 0 : device_state_bytes((int)gen);

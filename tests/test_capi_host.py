@@ -109,3 +109,16 @@ def test_prand_h_compiles_as_cpp(tmp_path):
 
 def test_prand_device_h_compiles_with_a_host_compiler(tmp_path):
     _compile_alone(tmp_path, "g++", "c++17", "prand_device.h", "cpp")
+
+
+def test_mt_jump_polynomials_match_the_oracle(lib):
+    # The library's host precomputation of x^(2^b) mod phi (Berlekamp-Massey,
+    # then squarings reduced eight coefficients per pass from byte tables)
+    # against the oracle's bit-serial squarings.  A wrong table entry, shift or
+    # pass order changes every later power.
+    import oracle as O
+    for b in (0, 1, 2, 31, 432, 511):
+        assert P.prand_mt_jump_polynomial(b) == O.mt_x_pow2k(b), b
+    buf = (ctypes.c_uint32 * 624)()
+    assert lib.prand_mt_jump_polynomial(512, ctypes.cast(buf, ctypes.c_void_p)) == 1
+    assert lib.prand_mt_jump_polynomial(0, None) == 1
