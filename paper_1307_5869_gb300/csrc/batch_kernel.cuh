@@ -166,6 +166,45 @@ __device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, 
 // words holding the state between polynomial applications; pbuf: 624 shared
 // words for the polynomial being applied; part: TEAM x 624 shared words for
 // the warps' partial results.
+// The outputs of an MT19937 tile made by the whole team: b0 holds the current
+// block (written by warp 0), idx the position inside it.  Each further block
+// is twisted by all TEAM warps (mt_twist_emit_team: TEAM chunks at a time
+// instead of one), so a long request's sequential work shrinks by about TEAM.
+template <typename OutT, int TEAM>
+__device__ __forceinline__ void batch_mt_emit_team(const BatchTile &T, const BatchCtx &C, uint32_t *b0, uint32_t *b1,
+                                                   uint32_t idx, int warp, int lane)
+{
+    __syncthreads();  // warp 0's copy of the current block is visible to the team
+    OutT *o = (OutT *)T.out;
+    const uint64_t nper = T.len;
+    uint64_t done = 0;
+    if (idx < (uint32_t)kMtN) {
+        const uint32_t cnt = (uint32_t)min((uint64_t)(kMtN - idx), nper);
+        for (uint32_t t = threadIdx.x; t < cnt; t += 32 * TEAM) o[t] = Cvt<OutT>::f(mt_temper(b0[idx + t]));
+        done = cnt;
+        idx += cnt;
+    }
+    bool in_b0 = true;
+    while (done < nper) {
+        const uint64_t rem = nper - done;
+        const uint32_t emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
+        if (in_b0) mt_twist_emit_team<OutT, TEAM>(b0, b1, warp, lane, o + done, emit);
+        else mt_twist_emit_team<OutT, TEAM>(b1, b0, warp, lane, o + done, emit);
+        done += emit;
+        idx = emit;
+        in_b0 = !in_b0;
+    }
+    if ((T.flags & kTileLast) && warp == 0) {
+        const uint32_t *cur = in_b0 ? b0 : b1;
+        uint32_t *d = (uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.wslot;
+        mt_copy_state_warp(cur, d, lane);
+        if (lane == 0) d[kMtN] = idx;
+    }
+    // every warp wrote outputs: each thread fences its own writes before the
+    // block barrier after which one thread publishes the tile's completion
+    __threadfence();
+}
+
 template <typename OutT, int TEAM>
 __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, uint32_t *ring, int ring_stride,
                                          uint32_t *tstate, uint32_t *pbuf, uint32_t *part, int warp, int lane)
@@ -194,6 +233,10 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
             mt_copy_state_warp(first ? src : tstate, b0, lane);
             __syncwarp();
         }
+    }
+    if constexpr (TEAM > 1) {
+        batch_mt_emit_team<OutT, TEAM>(T, C, b0, b1, idx, warp, lane);
+        return;
     }
     if (warp != 0) return;
     OutT *o = (OutT *)T.out;

@@ -71,6 +71,32 @@ __device__ __forceinline__ void mt_twist_emit_chunks(const uint32_t *__restrict_
     }
 }
 
+// The same twist by a team of TEAM warps that make up the whole block (TEAM
+// divides 20): in round r, warp w makes chunk TEAM r + w.  A chunk reads new
+// words only from chunks at least seven before it, i.e. from earlier rounds,
+// so one block barrier per round orders every such read after its write; a
+// final barrier publishes the new block.  All TEAM warps call it.
+template <typename OutT, int TEAM>
+__device__ __forceinline__ void mt_twist_emit_team(const uint32_t *__restrict__ ob, uint32_t *__restrict__ nb, int warp,
+                                                   int lane, OutT *o, uint32_t emit)
+{
+    static_assert(20 % TEAM == 0 && TEAM <= 4, "chunks per round");
+#pragma unroll
+    for (int r = 0; r < 20 / TEAM; ++r) {
+        const int c = TEAM * r + warp;
+        const int k = 32 * c + lane;
+        if (k < kMtN) {
+            const uint32_t a = ob[k];
+            const uint32_t b = k + 1 < kMtN ? ob[k + 1] : nb[0];
+            const uint32_t p = k < kMtN - kMtM ? ob[k + kMtM] : nb[k - (kMtN - kMtM)];
+            const uint32_t x = mt_recur(a, b, p);
+            nb[k] = x;
+            if ((uint32_t)k < emit) o[k] = Cvt<OutT>::f(mt_temper(x));
+        }
+        __syncthreads();
+    }
+}
+
 template <typename OutT>
 __device__ __forceinline__ void mt_twist_emit(const uint32_t *__restrict__ ob, uint32_t *__restrict__ nb, int lane,
                                               OutT *o, uint32_t emit)

@@ -471,11 +471,29 @@ prand_status_t prand_server_create(prand_server_t *out, uint64_t seed, uint64_t 
     S->seed = seed;
     prand_status_t s = batch_ctx(seed, 0, &S->ctx, nullptr);
     if (s != PRAND_OK) return fail(s);
+    // The tuned launch shape of this GPU, with the server's own section
+    // lengths: requests are short and latency counts, so 2048 outputs per lane
+    // for MRG32K3A / LFSR113 sections whatever the batch tuner chose for
+    // throughput (8192: p50 4.5 ms against 1.0 ms at the serving load).
     S->P = batch_params();
+    S->P.seclen_mrg_lfsr = 2048;
+    S->P.seclen_gm = 8192;
     S->out_cap = output_bytes & ~255ull;
     if (!dev_alloc(&S->out_base, S->out_cap)) { S->out_base = nullptr; return fail(PRAND_ERR_NOMEM); }
     S->arena = Arena(S->out_cap);
     S->slot_cap = slots_per_generator;
+    // Every resident stream holds a slot, so the map of resident streams never
+    // outgrows the slots: sized for them now, it is never rehashed under the
+    // lock while batches wait (a rehash of a few hundred thousand streams took
+    // tens of milliseconds in the middle of a serving run).  The same for the
+    // requests in the server at once and the streams moved to host memory.
+    try {
+        S->res.reserve((size_t)slots_per_generator * PRAND_NUM_GENERATORS);
+        S->reqs.reserve(2 * kFlights * kFlightReqs);
+        S->spilled.reserve((size_t)slots_per_generator * PRAND_NUM_GENERATORS);
+    } catch (const std::bad_alloc &) {
+        return fail(PRAND_ERR_NOMEM);
+    }
     for (int g = 0; g < PRAND_NUM_GENERATORS; ++g) {
         const size_t bytes = 2ull * slots_per_generator * slot_words(g) * 4;
         if (!dev_alloc(&S->slot_arena[g], bytes)) { S->slot_arena[g] = nullptr; return fail(PRAND_ERR_NOMEM); }

@@ -87,6 +87,23 @@ def test_server_alone_equals_in_the_mix():
         assert np.array_equal(alone[0].view(BITS[d]), mixed[i].view(BITS[d])), (g, k)
 
 
+def test_server_long_mt19937_requests_bit_exact():
+    # Long MT19937 requests (hundreds of 624-word blocks, generated by the
+    # tile's whole team of warps) and the short requests that continue their
+    # streams from the state they leave; ragged and whole last blocks, all
+    # dtypes, and stream 0 (no digits of the stream index at all).
+    rng = np.random.default_rng(12)
+    k1, k2 = (int(x) for x in rng.integers(0, 10**19, size=2, dtype=np.uint64))
+    reqs = [("MT19937", k1, (1 << 19) + 12345, 0),
+            ("MT19937", k1, 1000, 1),
+            ("MT19937", k2, 5 << 18, 2),
+            ("MT19937", k2, 700, 0),
+            ("MT19937", 0, (3 << 18) + 1, 1)]
+    outs, _ = _run(reqs, slots=8)
+    for (g, k, n, d), got, want in zip(reqs, outs, _expected(reqs)):
+        assert np.array_equal(got.view(BITS[d]), want.view(BITS[d])), (g, k, n, d)
+
+
 def test_server_replay_latencies():
     rng = np.random.default_rng(9)
     reqs = [(P.GENERATORS[i % 11], 0, int(rng.integers(0, 10**19, dtype=np.uint64)), 1024) for i in range(2000)]
