@@ -70,8 +70,8 @@ struct Engine {
     cudaEvent_t staged = nullptr;  // the last copy out of h_tiles
     uint32_t *d_counter = nullptr;
     BatchParams params;
-    int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // MT19937 (one warp per tile) and wide builds
-    int mt_team_bps = 1;                               // MT19937 build with a team of warps per tile
+    int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // the wide build's (the others keep their own)
+    int mt_team_bps = 1;                               // MT19937 build: a team of warps per tile
     int rest_bps[kRestVariants] = { 1, 1, 1, 1 };      // the rest build's variants
     cudaStream_t aux = nullptr;                   // second branch of mixed launches
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -95,12 +95,11 @@ prand_status_t engine_get(Engine **out)
         if (!dev_alloc(&E.d_counter, 64)) return PRAND_ERR_NOMEM;
         if (cudaEventCreateWithFlags(&E.staged, cudaEventDisableTiming) != cudaSuccess) return PRAND_ERR_CUDA;
         E.sms = device_sm_count();
-        for (int m : { (int)kModeMt, (int)kModeWide }) {
+        {
             int bps = 0;
-            const cudaError_t e = m == kModeMt
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeMt, 32, 128>, 32, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeWide, kBatchThreads, 128>, kBatchThreads, 0);
-            E.blocks_per_sm[m] = (e == cudaSuccess && bps >= 1) ? bps : 1;
+            const cudaError_t e =
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<kModeWide, kBatchThreads, 128>, kBatchThreads, 0);
+            E.blocks_per_sm[kModeWide] = (e == cudaSuccess && bps >= 1) ? bps : 1;
         }
         for (int v = 0; v < kRestVariants; ++v) E.rest_bps[v] = rest_blocks_per_sm(v);
         {
@@ -321,7 +320,7 @@ uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt)
 // the MT19937 part runs on `aux`, forked from and joined back into `st`.
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
                             uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux,
-                            cudaEvent_t fork, cudaEvent_t join, int mt_team)
+                            cudaEvent_t fork, cudaEvent_t join)
 {
     if (cudaMemsetAsync(d_counter, 0, 3 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
     if (!ntiles) return PRAND_OK;
@@ -336,13 +335,8 @@ prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t 
     if ((s = engine_get(&E)) != PRAND_OK) return s;
     if (nmt) {
         cudaStream_t ms = forked ? aux : st;
-        if (mt_team == kMtTeam) {
-            const unsigned g = batch_grid(nmt, 32, E->mt_team_bps);  // one tile per block
-            batch_kernel<kModeMt, 32 * kMtTeam, 128><<<g, 32 * kMtTeam, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
-        } else {
-            const unsigned g = batch_grid(nmt, 32, E->blocks_per_sm[kModeMt]);
-            batch_kernel<kModeMt, 32, 128><<<g, 32, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
-        }
+        const unsigned g = batch_grid(nmt, 32, E->mt_team_bps);  // one tile per block
+        batch_kernel<kModeMt, 32 * kMtTeam, 128><<<g, 32 * kMtTeam, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (nwide) {

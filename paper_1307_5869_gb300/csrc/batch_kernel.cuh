@@ -157,10 +157,9 @@ __device__ __forceinline__ void batch_gm(const BatchTile &T, const BatchCtx &C, 
 }
 
 // ------------------------------------------------------------------ MT19937 tiles
-// One tile = one request, run by a block of TEAM warps (1, or 4 where a
-// request's latency matters more than the batch's throughput): the team
-// applies the jump polynomials together (each warp owns a part of the 624
-// result words), then warp 0 generates the outputs.  Slot layout: 624 words of the current
+// One tile = one request, run by a block of TEAM warps: the team applies the
+// jump polynomials together (each warp takes a range of the coefficients),
+// then makes the outputs together (batch_mt_emit_team).  Slot layout: 624 words of the current
 // block, then the index inside it.  ring: the team's per-warp rings (2 x 624
 // words each, warp w at ring + w * ring_stride words); tstate: 624 shared
 // words holding the state between polynomial applications; pbuf: 624 shared
@@ -234,43 +233,7 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
             __syncwarp();
         }
     }
-    if constexpr (TEAM > 1) {
-        batch_mt_emit_team<OutT, TEAM>(T, C, b0, b1, idx, warp, lane);
-        return;
-    }
-    if (warp != 0) return;
-    OutT *o = (OutT *)T.out;
-    const uint64_t nper = T.len;
-    uint64_t done = 0;
-    if (idx < (uint32_t)kMtN) {
-        const uint32_t cnt = (uint32_t)min((uint64_t)(kMtN - idx), nper);
-        for (uint32_t t = lane; t < cnt; t += 32) o[t] = Cvt<OutT>::f(mt_temper(b0[idx + t]));
-        done = cnt;
-        idx += cnt;
-    }
-    bool in_b0 = true;
-    while (done < nper) {
-        uint64_t rem = nper - done;
-        uint32_t emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
-        mt_twist_emit<OutT>(b0, b1, lane, o + done, emit);
-        done += emit;
-        idx = emit;
-        in_b0 = false;
-        if (done >= nper) break;
-        rem = nper - done;
-        emit = rem < (uint64_t)kMtN ? (uint32_t)rem : (uint32_t)kMtN;
-        mt_twist_emit<OutT>(b1, b0, lane, o + done, emit);
-        done += emit;
-        idx = emit;
-        in_b0 = true;
-    }
-    if (T.flags & kTileLast) {
-        const uint32_t *cur = in_b0 ? b0 : b1;
-        uint32_t *d = (uint32_t *)C.slots[PRAND_MT19937] + (kMtN + 1) * (uint64_t)T.wslot;
-        mt_copy_state_warp(cur, d, lane);
-        if (lane == 0) d[kMtN] = idx;
-    }
-    __syncwarp();
+    batch_mt_emit_team<OutT, TEAM>(T, C, b0, b1, idx, warp, lane);
 }
 
 // ------------------------------------------------------------------ the persistent kernels
@@ -332,7 +295,7 @@ __global__ void __launch_bounds__(BS, (MODE == kModeRest ? 1280 / BS : MODE == k
     __shared__ __align__(16) unsigned char smem[BS / 32][WarpSmem<ROWB>::bytes];
     if constexpr (MODE == kModeMt) {
         constexpr int TEAM = BS / 32;  // one team of warps per block
-        static_assert(TEAM == 1 || TEAM == kMtTeam, "MT19937 builds: one warp or a team");
+        static_assert(TEAM == kMtTeam, "MT19937 build: one team of warps per tile");
         __shared__ uint32_t tstate[kMtN];
         __shared__ uint32_t pbuf[kMtPolyWords];
         __shared__ uint32_t part[TEAM > 1 ? TEAM * kMtN : 1];

@@ -380,8 +380,7 @@ bool launch_one(prand_server_s *S, Flight &F, int lane)
             cudaMemcpyAsync(F.d_tiles, F.h_tiles, n * sizeof(BatchTile), cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
             cudaMemcpyAsync(F.d_left, F.h_left, nr * 4, cudaMemcpyHostToDevice, F.st) != cudaSuccess ||
             launch_batch(F.d_tiles, (uint32_t)n, count_mt_tiles(tiles),
-                         count_wide_tiles(tiles, count_mt_tiles(tiles)), F.counter, ctx, F.st, nullptr, nullptr,
-                         nullptr, kMtTeam) != PRAND_OK ||
+                         count_wide_tiles(tiles, count_mt_tiles(tiles)), F.counter, ctx, F.st) != PRAND_OK ||
             cudaEventRecord(F.ev, F.st) != cudaSuccess)
             S->error = PRAND_ERR_CUDA;
     }
