@@ -283,7 +283,7 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
  * generation launch per request (no fusion, no persistent scheduling); the
  * comparison point for prand_batch_run.  Each stream is reached by the same
  * jump method the batched launch uses (for MT19937, one window polynomial per
- * nonzero hex digit of the stream index), so the two differ only in how the
+ * nonzero byte of the stream index), so the two differ only in how the
  * work is launched.  Returns after the work completes.
  * Errors: as prand_batch_run. */
 prand_status_t prand_batch_run_per_request(const prand_request_t *reqs, size_t n, uint64_t seed,

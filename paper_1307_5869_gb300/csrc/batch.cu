@@ -29,7 +29,7 @@ namespace prand {
 constexpr int kBatchThreads = 64;  // the wide build: small blocks (a warp on a long tile holds little besides itself)
 
 // One MT19937 stream for the per-request form: stream k = base advanced by
-// k 2^432, one window polynomial per nonzero hex digit of k (the same jump the
+// k 2^432, one window polynomial per nonzero byte of k (the same jump the
 // batched MT19937 tiles take), by one warp.
 __global__ void __launch_bounds__(32) mt_window_init_kernel(const uint32_t *base, const uint32_t *win, uint64_t k,
                                                             uint32_t *dst)
@@ -38,9 +38,10 @@ __global__ void __launch_bounds__(32) mt_window_init_kernel(const uint32_t *base
     const int lane = threadIdx.x;
     bool first = true;
     for (int i = 0; i < kMtWinPositions; ++i) {
-        const uint32_t d = (uint32_t)(k >> (4 * i)) & 15u;
+        const uint32_t d = (uint32_t)(k >> (kMtWinBits * i)) & (uint32_t)(kMtWinDigits - 1);
         if (!d) continue;
-        mt_apply_poly_warp(win + ((size_t)i * 16 + d) * kMtPolyWords, first ? base : dst, dst, seq, pbuf, lane);
+        mt_apply_poly_warp(win + ((size_t)i * kMtWinDigits + d) * kMtPolyWords, first ? base : dst, dst, seq, pbuf,
+                           lane);
         first = false;
         __syncwarp();
     }

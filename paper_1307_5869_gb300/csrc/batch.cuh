@@ -30,7 +30,7 @@ static_assert(sizeof(BatchTile) == 64, "tile layout");
 
 struct BatchCtx {
     const uint32_t *mrg_tab, *lfsr_tab, *mt_polys;
-    const uint32_t *mt_win;                  // stream jumps by hex digit: [16][16][624] (digit 0 unused)
+    const uint32_t *mt_win;                  // stream jumps by byte: [8][256][624] (digit 0 unused)
     const uint64_t *gm_tab[8];
     const void *base[PRAND_NUM_GENERATORS];  // base states of the batch's seed
     void *slots[PRAND_NUM_GENERATORS];       // resident-state arenas (server)

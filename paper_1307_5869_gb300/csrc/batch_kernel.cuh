@@ -218,13 +218,13 @@ __device__ __forceinline__ void batch_mt(const BatchTile &T, const BatchCtx &C, 
         }
         idx = src[kMtN];
     } else {
-        // stream k = base advanced by k 2^432: one polynomial per nonzero hex digit of k
+        // stream k = base advanced by k 2^432: one polynomial per nonzero byte of k
         const uint32_t *src = (const uint32_t *)C.base[PRAND_MT19937];
         bool first = true;
         for (int i = 0; i < kMtWinPositions; ++i) {
-            const uint32_t d = (uint32_t)(T.stream >> (4 * i)) & 15u;
+            const uint32_t d = (uint32_t)(T.stream >> (kMtWinBits * i)) & (uint32_t)(kMtWinDigits - 1);
             if (!d) continue;
-            mt_apply_poly_team<TEAM>(C.mt_win + ((size_t)i * 16 + d) * kMtPolyWords, first ? src : tstate, tstate,
+            mt_apply_poly_team<TEAM>(C.mt_win + ((size_t)i * kMtWinDigits + d) * kMtPolyWords, first ? src : tstate, tstate,
                                      ring + warp * ring_stride, pbuf, part, warp, lane);
             first = false;
         }

@@ -119,7 +119,7 @@ prand_status_t get_mt_window(DevTables *T)
     if (T->ready_mt_win) return PRAND_OK;
     const uint32_t *host = mt_host_window_polys();
     if (!host) return PRAND_ERR_STATE;
-    const size_t bytes = (size_t)kMtWinPositions * 16 * kMtPolyWords * sizeof(uint32_t);
+    const size_t bytes = (size_t)kMtWinPositions * kMtWinDigits * kMtPolyWords * sizeof(uint32_t);
     if (!dev_alloc(&T->mt_win, bytes)) return PRAND_ERR_NOMEM;
     if (cudaMemcpy(T->mt_win, host, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return PRAND_ERR_CUDA;
     T->ready_mt_win = true;

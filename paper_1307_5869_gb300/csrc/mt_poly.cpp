@@ -10,6 +10,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -282,30 +284,46 @@ void compute_window()
 {
     const uint32_t *pw = mt_host_pow2_polys();
     if (!pw) return;
-    g_win.assign((size_t)kMtWinPositions * 16 * kMtPolyWords, 0u);
+    constexpr int D = kMtWinDigits;
+    g_win.assign((size_t)kMtWinPositions * D * kMtPolyWords, 0u);
     const Reducer red(g_phi);
-    // position i: x^(d 2^(kMtStreamShift + 4 i)) mod phi for digits d = 1..15;
-    // the powers of two are stored already, the other digits are one product each
-    auto position = [&](int i) {
-        std::vector<Poly> P(16);
-        for (int t = 0; t < 4; ++t) P[(size_t)(1 << t)] = from_words(pw + (size_t)(kMtStreamShift + 4 * i + t) * kMtPolyWords);
-        for (int d = 3; d < 16; ++d) {
-            if ((d & (d - 1)) == 0) continue;
-            const int hi = 1 << (31 - __builtin_clz((unsigned)d));
-            P[(size_t)d].assign((size_t)kW, 0);
-            mul_into(P[(size_t)hi], P[(size_t)(d - hi)], P[(size_t)d], red);
-        }
-        for (int d = 1; d < 16; ++d) {
-            uint32_t *dst = g_win.data() + ((size_t)i * 16 + d) * kMtPolyWords;
+    // P[i][d] = x^(d 2^(kMtStreamShift + 8 i)) mod phi.  The powers of two are
+    // stored already; every other digit d is one product, of its highest bit
+    // 2^b and of d - 2^b < 2^b, so the digits with the same highest bit form a
+    // wave whose products are independent and run on all host threads.
+    std::vector<std::vector<Poly>> P((size_t)kMtWinPositions, std::vector<Poly>((size_t)D));
+    for (int i = 0; i < kMtWinPositions; ++i)
+        for (int t = 0; t < kMtWinBits; ++t)
+            P[(size_t)i][(size_t)(1 << t)] = from_words(pw + (size_t)(kMtStreamShift + kMtWinBits * i + t) * kMtPolyWords);
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nth = (int)std::max(1u, std::min(hw ? hw : 1u, 64u));
+    for (int b = 1; b < kMtWinBits; ++b) {
+        std::vector<std::pair<int, int>> items;  // (position, digit) of this wave
+        for (int i = 0; i < kMtWinPositions; ++i)
+            for (int d = (1 << b) + 1; d < (2 << b); ++d) items.emplace_back(i, d);
+        std::atomic<size_t> next(0);
+        auto work = [&]() {
+            for (size_t k; (k = next.fetch_add(1)) < items.size();) {
+                const int i = items[k].first, d = items[k].second;
+                Poly &out = P[(size_t)i][(size_t)d];
+                out.assign((size_t)kW, 0);
+                mul_into(P[(size_t)i][(size_t)(1 << b)], P[(size_t)i][(size_t)(d - (1 << b))], out, red);
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nth && (size_t)t < items.size(); ++t) th.emplace_back(work);
+        work();
+        for (std::thread &t : th) t.join();
+    }
+    for (int i = 0; i < kMtWinPositions; ++i)
+        for (int d = 1; d < D; ++d) {
+            uint32_t *dst = g_win.data() + ((size_t)i * D + d) * kMtPolyWords;
+            const Poly &src = P[(size_t)i][(size_t)d];
             for (int k = 0; k < kMtPolyWords / 2; ++k) {
-                dst[2 * k] = (uint32_t)P[(size_t)d][(size_t)k];
-                dst[2 * k + 1] = (uint32_t)(P[(size_t)d][(size_t)k] >> 32);
+                dst[2 * k] = (uint32_t)src[(size_t)k];
+                dst[2 * k + 1] = (uint32_t)(src[(size_t)k] >> 32);
             }
         }
-    };
-    std::vector<std::thread> th;
-    for (int i = 0; i < kMtWinPositions; ++i) th.emplace_back(position, i);
-    for (std::thread &t : th) t.join();
     g_win_ok = true;
 }
 }  // namespace

@@ -47,7 +47,9 @@ constexpr int kMtDeg = 19937;          // state dimension over GF(2)
 constexpr int kMtPolyWords = 624;      // 32-bit words per jump polynomial (19968 bits)
 constexpr int kMtPolyCount = 512;      // stored x^(2^b) mod phi, b = 0..511 (Sec. 5.4)
 constexpr int kMtStreamShift = 432;    // L = 2^432 >= 1e130 (Table 4)
-constexpr int kMtWinPositions = 16;    // hex digits of a 64-bit stream index
+constexpr int kMtWinBits = 8;          // stream jumps by digits of 8 bits (bytes) of the stream index
+constexpr int kMtWinDigits = 1 << kMtWinBits;
+constexpr int kMtWinPositions = 64 / kMtWinBits;  // digit positions of a 64-bit stream index
 
 // MRG32K3A (Sec. 5.2).
 constexpr uint32_t kM1 = 4294967087u;  // 2^32 - 209
@@ -116,7 +118,7 @@ struct DevTables {
     uint32_t *lfsr = nullptr;     // [4][kJumpBits][32]: column images of T_c^(2^b)
     uint64_t *gm[8] = {};         // per GM/GQ generator: [kJumpBits][4] = M^(2^b) mod p
     uint32_t *mt = nullptr;       // [kMtPolyCount][kMtPolyWords]: x^(2^b) mod phi
-    uint32_t *mt_win = nullptr;   // [16][16][kMtPolyWords]: x^(d 2^(432 + 4 i)) mod phi, digit d of position i
+    uint32_t *mt_win = nullptr;   // [kMtWinPositions][kMtWinDigits][kMtPolyWords]: x^(d 2^(432 + 8 i)) mod phi
     bool ready_basic = false;
     bool ready_mt = false;
     bool ready_mt_win = false;
@@ -129,9 +131,11 @@ prand_status_t get_tables(int gen, DevTables **out);
 // and the squaring chain x^(2^b) mod phi, b < count; each polynomial as 624
 // little-endian 32-bit words.  Computed once per process.
 const uint32_t *mt_host_pow2_polys();
-// x^(d 2^(432 + 4 i)) mod phi for the 16 hex-digit positions i of a stream
-// index and digits d = 1..15 ([i][d][624 words], d = 0 unused): a stream jump
-// is one polynomial application per nonzero digit.  Computed once per process.
+// x^(d 2^(432 + 8 i)) mod phi for the 8 byte positions i of a stream index and
+// digits d = 1..255 ([i][d][624 words], d = 0 unused): a stream jump is one
+// polynomial application per nonzero byte (about 8 for a random 64-bit index,
+// against about 15 with hex digits).  Computed once per process, on all host
+// cores.
 const uint32_t *mt_host_window_polys();
 // The device copy of that table for the current device (built on first use).
 prand_status_t get_mt_window(DevTables *T);
