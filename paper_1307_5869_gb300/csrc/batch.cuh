@@ -70,7 +70,8 @@ uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt);
 // Warps per MT19937 tile: the team applies each jump polynomial together
 // (each warp takes a quarter of its coefficients) and then twists each output
 // block together (five rounds of four 32-word chunks), for batches and the
-// server alike (one warp per tile: C4 23.1 ms against 19.3 ms).
+// server alike (a batch of 10^4 mixed requests ran 16 % faster so than with
+// one warp per tile).
 constexpr int kMtTeam = 4;
 
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
