@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "mrg_lfsr_dev.cuh"
 
@@ -32,9 +33,15 @@ struct LfsrSecJumps {
     static constexpr int kCount = kSecJumps;
     uint32_t col[kSecJumps][4][32];  // [s - 1][component][bit]: image of bit i under T_c^(s seclen)
 };
+// MRG32K3A: section s < 16^4 reached by one matrix per nonzero base-16 digit
+// d_j of s (A^(d_j 16^j seclen) commute, so their order does not matter): at
+// most four 3x3 products however many sections a fill has, so a single stream
+// can be split into sections of 64 outputs (one table entry per set bit of the
+// offset would cost up to 14 dependent products per section).
 struct MrgSecJumps {
-    static constexpr int kCount = kSecJumps;
-    uint32_t m[kSecJumps][18];  // [s - 1]: A^(s seclen) mod m1, B^(s seclen) mod m2, row-major
+    static constexpr int kLevels = 4;
+    static constexpr uint32_t kMaxSections = 1u << (4 * kLevels);
+    uint32_t m[kLevels][15][18];  // [j][d - 1]: A^(d 16^j seclen) mod m1, B^(...) mod m2, row-major
 };
 
 template <typename SJ>
@@ -55,10 +62,16 @@ template <typename SJ>
 __device__ __forceinline__ void mrg_jump_section(const uint32_t *tab, const SJ &sj, uint64_t sec, uint64_t start,
                                                  uint32_t x[3], uint32_t y[3])
 {
-    if constexpr (SJ::kCount > 0) {
-        if (sec <= (uint64_t)SJ::kCount) {
-            mat3_vec<209>(sj.m[sec - 1], x);
-            mat3_vec<22853>(sj.m[sec - 1] + 9, y);
+    if constexpr (!std::is_same<SJ, NoSecJumps>::value) {
+        if (sec < (uint64_t)SJ::kMaxSections) {
+#pragma unroll
+            for (int j = 0; j < SJ::kLevels; ++j) {
+                const uint32_t d = (uint32_t)(sec >> (4 * j)) & 15u;
+                if (d) {
+                    mat3_vec<209>(sj.m[j][d - 1], x);
+                    mat3_vec<22853>(sj.m[j][d - 1] + 9, y);
+                }
+            }
             return;
         }
     }
@@ -446,15 +459,20 @@ void build_sec_jumps(uint64_t seclen, uint32_t nsec, MrgSecJumps *out)
     const Mat3 b = { 527612, 0, kM2 - 1370589, 1, 0, 0, 0, 1, 0 };
     auto mul1 = [](const Mat3 &X, const Mat3 &Y) { return mat3_mul(X, Y, kM1); };
     auto mul2 = [](const Mat3 &X, const Mat3 &Y) { return mat3_mul(X, Y, kM2); };
-    const Mat3 A = mat_pow(a, seclen, one, mul1), B = mat_pow(b, seclen, one, mul2);
-    Mat3 JA = A, JB = B;
-    for (uint32_t s = 1; s < nsec && s <= (uint32_t)kSecJumps; ++s) {
-        for (int i = 0; i < 9; ++i) {
-            out->m[s - 1][i] = (uint32_t)JA[i];
-            out->m[s - 1][9 + i] = (uint32_t)JB[i];
+    (void)nsec;
+    Mat3 A = mat_pow(a, seclen, one, mul1), B = mat_pow(b, seclen, one, mul2);  // A^(16^j seclen)
+    for (int j = 0; j < MrgSecJumps::kLevels; ++j) {
+        Mat3 JA = A, JB = B;
+        for (int d = 1; d < 16; ++d) {
+            for (int i = 0; i < 9; ++i) {
+                out->m[j][d - 1][i] = (uint32_t)JA[i];
+                out->m[j][d - 1][9 + i] = (uint32_t)JB[i];
+            }
+            JA = mul1(JA, A);
+            JB = mul2(JB, B);
         }
-        JA = mul1(JA, A);
-        JB = mul2(JB, B);
+        A = JA;  // (A^(16^j seclen))^16
+        B = JB;
     }
 }
 
@@ -478,12 +496,15 @@ void sec_jumps(std::map<std::tuple<int, uint64_t, uint32_t>, SJ> &cache, int gen
 }  // namespace
 
 // Sections per stream: whole waves of the kernel's resident threads (cap),
-// sections no shorter than 256 outputs and starting on multiples of 32
-// outputs, so the staged 128-byte row stores of every section fill whole
-// cache lines.
-static void pick_sections(uint64_t nstreams, uint64_t nper, uint64_t cap, uint32_t *nsec, uint64_t *seclen)
+// sections no shorter than min_len outputs (256 for LFSR113, whose section
+// jumps beyond the 15 tabulated ones take one table entry per set bit of the
+// offset; 64 for MRG32K3A, whose take at most four products) and starting on
+// multiples of 32 outputs, so the staged 128-byte row stores of every section
+// fill whole cache lines.
+static void pick_sections(uint64_t nstreams, uint64_t nper, uint64_t cap, uint64_t min_len, uint32_t *nsec,
+                          uint64_t *seclen)
 {
-    const uint32_t s = pick_nsec(nstreams, cap, nper / 256, nper);
+    const uint32_t s = pick_nsec(nstreams, cap, nper / min_len, nper);
     uint64_t len = (nper + s - 1) / s;
     len = (len + 31) & ~31ull;
     if (len == 0) len = 32;
@@ -501,7 +522,7 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
         // size by the rows form (the other form has the same footprint or less)
         const uint64_t cap = gen == PRAND_MRG32K3A ? resident_threads<1>(mrg_gen_kernel<OutT, true>)
                                                    : resident_threads<2, kLfsrBlock>(lfsr_gen_kernel<OutT, true>);
-        pick_sections(R.count, nper, cap, &R.nsec, &R.seclen);
+        pick_sections(R.count, nper, cap, gen == PRAND_MRG32K3A ? 64 : 256, &R.nsec, &R.seclen);
     }
     const uint32_t nsec = R.nsec;
     const uint64_t seclen = R.seclen, nstreams = R.count;
@@ -513,7 +534,7 @@ static prand_status_t mrg_lfsr_gen_t(int gen, const DevTables *T, void *d_state,
     constexpr uint64_t E = RowFill<OutT>::E;
     const bool rows = ((uintptr_t)out % 16) == 0 && nper % E == 0 && seclen % E == 0;
     // section jumps as one matrix per section when there are few sections
-    const bool sj = nsec > 1 && nsec <= (uint32_t)kSecJumps + 1;
+    const bool sj = nsec > 1 && (gen == PRAND_MRG32K3A ? nsec <= MrgSecJumps::kMaxSections : nsec <= (uint32_t)kSecJumps + 1);
     if (gen == PRAND_MRG32K3A) {
         const unsigned g = grid_for(threads, B);
         if (sj) {
@@ -663,9 +684,11 @@ extern "C" prand_status_t prand_mrg32k3a_generate_u32_noalloc(uint32_t *dev_stat
     if (n_per_stream == 0) return PRAND_OK;
     uint32_t nsec;
     uint64_t seclen;
-    // the same section choice and store form as prand_generate_u32 on a handle:
-    // staged 128-byte row stores whenever every row start is 16-byte aligned
-    pick_sections(n_streams, n_per_stream, resident_threads<1>(mrg_gen_kernel<uint32_t, true>), &nsec, &seclen);
+    // the store form of prand_generate_u32 on a handle (staged 128-byte row
+    // stores whenever every row start is 16-byte aligned); sections of at least
+    // 256 outputs, since this path builds no section matrices (that would
+    // allocate host memory) and jumps by one table entry per set bit
+    pick_sections(n_streams, n_per_stream, resident_threads<1>(mrg_gen_kernel<uint32_t, true>), 256, &nsec, &seclen);
     int vec = ((uintptr_t)dev_out % 16) == 0;
     constexpr uint64_t E = RowFill<uint32_t>::E;
     const bool rows = vec && n_per_stream % E == 0 && seclen % E == 0;
