@@ -59,7 +59,7 @@ LANES_PER_SM = 128
 # at 2^18 streams x 2^10 outputs, scaled per stream; None for other shapes.
 TRAFFIC_PER_STREAM_1024 = {"MT19937.u32": 2.322e9 / 2**18, "MT19937.f32": 2.319e9 / 2**18,
                            "LFSR113.u32": 1.025e9 / 2**18, "LFSR113.f32": 1.022e9 / 2**18,
-                           "GM61.u32": 1.396e9 / 2**18, "GM61.f32": 1.394e9 / 2**18}
+                           "GM61.u32": 1.396e9 / 2**18, "GM61.f32": 1.395e9 / 2**18}
 # Output arena of the serving leg: 32 GiB of the GPU's HBM holds every request's
 # output until it is read (at 1.9e10 samples/s of 4-8 byte samples, about a
 # third of a second of demand).
