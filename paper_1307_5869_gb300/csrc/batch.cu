@@ -74,8 +74,7 @@ struct Engine {
     int sms = 1, blocks_per_sm[kModes] = { 1, 1, 1 };  // the wide build's (the others keep their own)
     int mt_team_bps = 1;                               // MT19937 build: a team of warps per tile
     int rest_bps[kRestVariants] = { 1, 1, 1, 1 };      // the rest build's variants
-    cudaStream_t aux = nullptr;                   // second branch of mixed launches
-    cudaEvent_t fork = nullptr, join = nullptr;
+    Branches br;                                  // side branches of mixed launches
     std::mutex aux_mu;
     bool ready = false;
 };
@@ -109,10 +108,7 @@ prand_status_t engine_get(Engine **out)
                 &bps, batch_kernel<kModeMt, 32 * kMtTeam, 128>, 32 * kMtTeam, 0);
             E.mt_team_bps = (e == cudaSuccess && bps >= 1) ? bps : 1;
         }
-        if (cudaStreamCreateWithFlags(&E.aux, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&E.fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&E.join, cudaEventDisableTiming) != cudaSuccess)
-            return PRAND_ERR_CUDA;
+        if (E.br.create() != PRAND_OK) return PRAND_ERR_CUDA;
         const char *path = getenv("PRAND_TUNE_CACHE");
         if (path) {
             FILE *f = fopen(path, "r");
@@ -318,32 +314,54 @@ uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt)
 
 // Tiles [0, nmt): MT19937 (counter[0]); [nmt, nmt + nwide): thread-per-stream
 // GM/GQ (counter[2]); the rest (counter[1]).  With MT19937 tiles beside others
-// the MT19937 part runs on `aux`, forked from and joined back into `st`.
+// with side branches the MT19937 part runs on br->st[0] and the
+// thread-per-stream part on br->st[1], each forked from and joined back into `st`.
+prand_status_t Branches::create()
+{
+    for (int b = 0; b < 2; ++b)
+        if (cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join[b], cudaEventDisableTiming) != cudaSuccess)
+            return PRAND_ERR_CUDA;
+    return PRAND_OK;
+}
+
+void Branches::destroy()
+{
+    for (int b = 0; b < 2; ++b) {
+        if (st[b]) cudaStreamDestroy(st[b]);
+        if (fork[b]) cudaEventDestroy(fork[b]);
+        if (join[b]) cudaEventDestroy(join[b]);
+        st[b] = nullptr;
+        fork[b] = join[b] = nullptr;
+    }
+}
+
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
-                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux,
-                            cudaEvent_t fork, cudaEvent_t join)
+                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, const Branches *br)
 {
     if (cudaMemsetAsync(d_counter, 0, 3 * sizeof(uint32_t), st) != cudaSuccess) return PRAND_ERR_CUDA;
     if (!ntiles) return PRAND_OK;
     const uint32_t nrest = ntiles - nmt - nwide;
-    const bool forked = nmt && (nwide || nrest);
+    // a part goes to its branch when another part runs beside it
+    const bool on_branch[2] = { br && nmt && (nwide || nrest), br && nwide && nrest };
     prand_status_t s = PRAND_OK;
-    if (forked) {
-        if (!aux || cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(aux, fork, 0) != cudaSuccess)
+    for (int b = 0; b < 2; ++b)
+        if (on_branch[b] && (cudaEventRecord(br->fork[b], st) != cudaSuccess ||
+                             cudaStreamWaitEvent(br->st[b], br->fork[b], 0) != cudaSuccess))
             return PRAND_ERR_CUDA;
-    }
     Engine *E;
     if ((s = engine_get(&E)) != PRAND_OK) return s;
     if (nmt) {
-        cudaStream_t ms = forked ? aux : st;
+        cudaStream_t ms = on_branch[0] ? br->st[0] : st;
         const unsigned g = batch_grid(nmt, 32, E->mt_team_bps);  // one tile per block
         batch_kernel<kModeMt, 32 * kMtTeam, 128><<<g, 32 * kMtTeam, 0, ms>>>(d_tiles, nmt, d_counter, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (nwide) {
         const unsigned g = batch_grid(nwide, kBatchThreads, E->blocks_per_sm[kModeWide]);
-        batch_kernel<kModeWide, kBatchThreads, 128><<<g, kBatchThreads, 0, st>>>(d_tiles + nmt, nwide, d_counter + 2,
-                                                                               ctx);
+        batch_kernel<kModeWide, kBatchThreads, 128><<<g, kBatchThreads, 0, on_branch[1] ? br->st[1] : st>>>(
+            d_tiles + nmt, nwide, d_counter + 2, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
     if (nrest) {
@@ -352,8 +370,10 @@ prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t 
                     d_counter + 1, ctx);
         if ((s = launch_check()) != PRAND_OK) return s;
     }
-    if (forked && (cudaEventRecord(join, aux) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess))
-        return PRAND_ERR_CUDA;
+    for (int b = 0; b < 2; ++b)
+        if (on_branch[b] && (cudaEventRecord(br->join[b], br->st[b]) != cudaSuccess ||
+                             cudaStreamWaitEvent(st, br->join[b], 0) != cudaSuccess))
+            return PRAND_ERR_CUDA;
     return PRAND_OK;
 }
 
@@ -395,8 +415,7 @@ struct prand_batch_plan_s {
     int device = -1;
     BatchTile *d_tiles = nullptr;
     uint32_t ntiles = 0, nmt = 0, nwide = 0;
-    cudaStream_t aux = nullptr;  // the second branch while capturing
-    cudaEvent_t fork = nullptr, join = nullptr;
+    Branches br;  // the side branches while capturing
     uint32_t *d_counter = nullptr;
     BatchCtx ctx;
     cudaGraph_t graph = nullptr;
@@ -423,10 +442,9 @@ prand_status_t prand_batch_run(const prand_request_t *reqs, size_t n, uint64_t s
     if ((s = upload_tiles(tiles, st, &d_tiles, &counter)) != PRAND_OK) return s;
     Engine *E;
     if ((s = engine_get(&E)) != PRAND_OK) return s;
-    std::lock_guard<std::mutex> lk(E->aux_mu);  // one user of the second branch at a time
+    std::lock_guard<std::mutex> lk(E->aux_mu);  // one user of the branches at a time
     const uint32_t nmt = count_mt_tiles(tiles);
-    return launch_batch(d_tiles, (uint32_t)tiles.size(), nmt, count_wide_tiles(tiles, nmt), counter, ctx, st, E->aux,
-                        E->fork, E->join);
+    return launch_batch(d_tiles, (uint32_t)tiles.size(), nmt, count_wide_tiles(tiles, nmt), counter, ctx, st, &E->br);
 }
 
 prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_request_t *reqs, size_t n, uint64_t seed)
@@ -441,9 +459,7 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     cudaStream_t cap = nullptr;
     auto fail = [&](prand_status_t e) {
         if (cap) cudaStreamDestroy(cap);
-        if (p->aux) cudaStreamDestroy(p->aux);
-        if (p->fork) cudaEventDestroy(p->fork);
-        if (p->join) cudaEventDestroy(p->join);
+        p->br.destroy();
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);
         if (p->d_tiles) cudaFree(p->d_tiles);
@@ -461,22 +477,18 @@ prand_status_t prand_batch_plan_create(prand_batch_plan_t *out, const prand_requ
     p->nmt = count_mt_tiles(tiles);
     p->nwide = count_wide_tiles(tiles, p->nmt);
     if (!dev_alloc(&p->d_counter, 64)) return fail(PRAND_ERR_NOMEM);
-    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming) != cudaSuccess)
-        return fail(PRAND_ERR_CUDA);
+    if (p->br.create() != PRAND_OK) return fail(PRAND_ERR_CUDA);
     if (p->ntiles) {
         if (!dev_alloc(&p->d_tiles, tiles.size() * sizeof(BatchTile))) return fail(PRAND_ERR_NOMEM);
         if (cudaMemcpy(p->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(PRAND_ERR_CUDA);
     }
     if (cudaStreamSynchronize(0) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-    // capture: counter reset + the persistent launches (the MT19937 branch forked
-    // onto the plan's second stream and joined back)
+    // capture: counter reset + the persistent launches (the MT19937 and
+    // thread-per-stream parts forked onto the plan's branch streams and joined back)
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return fail(PRAND_ERR_CUDA);
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(PRAND_ERR_CUDA);
-    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->nmt, p->nwide, p->d_counter, p->ctx, cap, p->aux,
-                                     p->fork, p->join);
+    prand_status_t ls = launch_batch(p->d_tiles, p->ntiles, p->nmt, p->nwide, p->d_counter, p->ctx, cap, &p->br);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cap, &g);
     p->graph = g;
@@ -505,9 +517,7 @@ prand_status_t prand_batch_plan_destroy(prand_batch_plan_t p)
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->d_counter) cudaFree(p->d_counter);
-    if (p->aux) cudaStreamDestroy(p->aux);
-    if (p->fork) cudaEventDestroy(p->fork);
-    if (p->join) cudaEventDestroy(p->join);
+    p->br.destroy();
     delete p;
     return PRAND_OK;
 }

@@ -61,9 +61,16 @@ prand_status_t validate_requests(const prand_request_t *reqs, size_t n);
 // nwide) the thread-per-stream GM/GQ tiles (GM55, GQ58.3, GQ58.4: their points
 // need more registers than the last build allows), then every other generator
 // (few registers, many resident warps).  order_tiles puts them in that order.
-// When MT19937 tiles share a list with others they run on `aux`, forked from
-// and joined into `st` with the two events; the other two parts run one after
-// the other on `st`, so a list without MT19937 tiles needs no second stream.
+// With side branches (Branches), the MT19937 part and the thread-per-stream
+// part each run on a branch stream of their own, forked from and joined back
+// into `st`, so all three builds share the GPU at once; without them (the
+// server's flights, one stream each) the parts run one after the other.
+struct Branches {
+    cudaStream_t st[2] = {};  // [0] MT19937 tiles, [1] thread-per-stream GM/GQ tiles
+    cudaEvent_t fork[2] = {}, join[2] = {};
+    prand_status_t create();
+    void destroy();
+};
 bool wide_tile_gen(int gen);
 uint32_t count_mt_tiles(const std::vector<BatchTile> &tiles);
 uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt);
@@ -75,7 +82,6 @@ uint32_t count_wide_tiles(const std::vector<BatchTile> &tiles, uint32_t nmt);
 constexpr int kMtTeam = 4;
 
 prand_status_t launch_batch(const BatchTile *d_tiles, uint32_t ntiles, uint32_t nmt, uint32_t nwide,
-                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, cudaStream_t aux = nullptr,
-                            cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                            uint32_t *d_counter, const BatchCtx &ctx, cudaStream_t st, const Branches *br = nullptr);
 
 }  // namespace prand
